@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against facts fixed by the mathematics.
+
+Each test checks the oracle against something other than itself: a closed
+form, a dense LAPACK solve, textbook CG, an exact identity of the operator,
+or brute force on a tiny case. Together they are chosen so that a dropped
+term, a wrong sign, a wrong index or a transposed link fails at least one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1102_2143_gb300 import inputs
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _vec(n, seed):
+    return inputs.gaussian_source(n, seed)
+
+
+# ----------------------------------------------------------------------------
+# Operator structure (staggered D, A = m^2 - D^2)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_dslash_is_anti_hermitian(nc):
+    dims = (4, 4, 6, 4)
+    U = inputs.su_n_links(dims, nc, 0.7, 11)
+    n = inputs.volume(dims) * nc
+    u, v = _vec(n, 1), _vec(n, 2)
+    Du = oracle.dslash(U, dims, nc, u)
+    Dv = oracle.dslash(U, dims, nc, v)
+    lhs = np.vdot(u, Dv)
+    rhs = -np.vdot(Du, v)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+    # <v, D v> purely imaginary
+    q = np.vdot(v, Dv)
+    assert abs(q.real) <= 1e-13 * np.linalg.norm(v) ** 2
+
+
+def test_a_hermitian_positive():
+    dims, nc, m = (4, 4, 4, 4), 3, 0.1
+    U = inputs.su_n_links(dims, nc, 0.9, 12)
+    n = inputs.volume(dims) * nc
+    u, v = _vec(n, 3), _vec(n, 4)
+    Au = oracle.staggered_apply(U, dims, nc, m, u)
+    Av = oracle.staggered_apply(U, dims, nc, m, v)
+    assert abs(np.vdot(u, Av) - np.vdot(Au, v)) <= 1e-13 * abs(np.vdot(u, Av))
+    Dv = oracle.dslash(U, dims, nc, v)
+    vAv = np.vdot(v, Av)
+    assert abs(vAv.imag) <= 1e-13 * abs(vAv)
+    # <v, A v> = m^2 |v|^2 + |D v|^2  >=  m^2 |v|^2
+    expect = m * m * np.linalg.norm(v) ** 2 + np.linalg.norm(Dv) ** 2
+    assert abs(vAv.real - expect) <= 1e-12 * expect
+    assert vAv.real >= m * m * np.linalg.norm(v) ** 2
+
+
+def _unit(n, i):
+    e = np.zeros(n, dtype=np.complex128)
+    e[i] = 1.0
+    return e
+
+
+def _site(x, dims):
+    return x[0] + dims[0] * (x[1] + dims[1] * (x[2] + dims[2] * x[3]))
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_a_blocks_diagonal_and_two_hop(nc):
+    """A_xx = (m^2 + 2) I for unitary links; the block coupling x to x+2mu is
+    -1/4 U_mu(x) U_mu(x+mu) (the single two-hop path); that to x+mu+nu is the
+    sum of the two paths with the staggered phases."""
+    dims, m = (6, 6, 6, 6), 0.3
+    U = inputs.su_n_links(dims, nc, 0.8, 13)
+    n = inputs.volume(dims) * nc
+    x = (1, 2, 3, 4)
+    sx = _site(x, dims)
+    for mu in range(4):
+        xp = list(x); xp[mu] = (xp[mu] + 1) % dims[mu]
+        x2 = list(x); x2[mu] = (x2[mu] + 2) % dims[mu]
+        s1, s2 = _site(xp, dims), _site(x2, dims)
+        blk = np.zeros((nc, nc), dtype=np.complex128)
+        for b in range(nc):
+            col = oracle.staggered_apply(U, dims, nc, m, _unit(n, s2 * nc + b))
+            blk[:, b] = col[sx * nc:(sx + 1) * nc]
+        expect = -0.25 * U[mu, sx] @ U[mu, s1]
+        assert np.max(np.abs(blk - expect)) <= 1e-14
+    diag = np.zeros((nc, nc), dtype=np.complex128)
+    for b in range(nc):
+        col = oracle.staggered_apply(U, dims, nc, m, _unit(n, sx * nc + b))
+        diag[:, b] = col[sx * nc:(sx + 1) * nc]
+    assert np.max(np.abs(diag - (m * m + 2.0) * np.eye(nc))) <= 1e-14
+    # x -> x + e0 + e1: paths via x+e0 and via x+e1.
+    # eta_0 = 1; eta_1(x) = (-1)^x0.
+    def eta(y, mu):
+        return (-1) ** (sum(y[:mu]) % 2)
+    y0 = list(x); y0[0] += 1
+    y1 = list(x); y1[1] += 1
+    z = list(x); z[0] += 1; z[1] += 1
+    sz, sy0, sy1 = _site(z, dims), _site(y0, dims), _site(y1, dims)
+    blk = np.zeros((nc, nc), dtype=np.complex128)
+    for b in range(nc):
+        col = oracle.staggered_apply(U, dims, nc, m, _unit(n, sz * nc + b))
+        blk[:, b] = col[sx * nc:(sx + 1) * nc]
+    expect = -0.25 * (eta(x, 0) * eta(y0, 1) * U[0, sx] @ U[1, sy0]
+                      + eta(x, 1) * eta(y1, 0) * U[1, sx] @ U[0, sy1])
+    assert np.max(np.abs(blk - expect)) <= 1e-14
+
+
+def _free_field_solution(b, dims, nc, m, sigma):
+    """(m^2 + sigma - D^2)^{-1} b for U = 1 in momentum space: the staggered
+    phases make the cross terms of D^2 cancel, leaving
+    -D^2 = sum_mu sin^2(p_mu), p_mu = 2 pi k / L_mu."""
+    L0, L1, L2, L3 = dims
+    bb = b.reshape(L3, L2, L1, L0, nc)
+    bh = np.fft.fftn(bb, axes=(0, 1, 2, 3))
+    k = [2 * np.pi * np.fft.fftfreq(L) for L in (L3, L2, L1, L0)]
+    P = np.meshgrid(*k, indexing="ij")
+    lam = m * m + sigma + sum(np.sin(p) ** 2 for p in P)
+    xh = bh / lam[..., None]
+    return np.fft.ifftn(xh, axes=(0, 1, 2, 3)).reshape(-1)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (4, 6, 2, 8)])
+def test_free_field_closed_form(dims):
+    nc, m = 3, 0.2
+    U = inputs.su_n_links(dims, nc, 0.0, 14)
+    assert np.all(U == np.eye(nc))
+    n = inputs.volume(dims) * nc
+    b = _vec(n, 5)
+    sig = inputs.log_shifts(1e-2, 1.0, 4)
+    for s in sig:
+        xs = _free_field_solution(b, dims, nc, m, s)
+        # the oracle's operator maps the closed-form solution back to b
+        back = oracle.staggered_apply(U, dims, nc, m, xs, sigma=s)
+        assert np.linalg.norm(back - b) <= 1e-13 * np.linalg.norm(b)
+    res = oracle.cgm_staggered(U, dims, nc, m, b, sig, 1e-13)
+    assert res.status == 0
+    for i, s in enumerate(sig):
+        xs = _free_field_solution(b, dims, nc, m, s)
+        assert np.linalg.norm(res.x[i] - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_gauge_covariance():
+    """U'_mu(x) = g(x) U_mu(x) g(x+mu)^dagger gives A' = G A G^dagger."""
+    dims, nc, m = (4, 4, 4, 6), 3, 0.15
+    U = inputs.su_n_links(dims, nc, 0.6, 15)
+    g = inputs.random_gauge(dims, nc, 16)
+    V = inputs.volume(dims)
+    Up = np.empty_like(U)
+    for mu in range(4):
+        sites = np.arange(V)
+        coords = np.stack(np.unravel_index(sites, (dims[3], dims[2], dims[1], dims[0]))[::-1], 1)
+        c2 = coords.copy()
+        c2[:, mu] = (c2[:, mu] + 1) % dims[mu]
+        fwd = c2[:, 0] + dims[0] * (c2[:, 1] + dims[1] * (c2[:, 2] + dims[2] * c2[:, 3]))
+        Up[mu] = g @ U[mu] @ np.conj(np.swapaxes(g[fwd], 1, 2))
+    n = V * nc
+    v = _vec(n, 6)
+    Gv = (g @ v.reshape(V, nc, 1)).reshape(-1)
+    lhs = oracle.staggered_apply(Up, dims, nc, m, Gv)
+    rhs = (g @ oracle.staggered_apply(U, dims, nc, m, v).reshape(V, nc, 1)).reshape(-1)
+    assert np.linalg.norm(lhs - rhs) <= 1e-13 * np.linalg.norm(rhs)
+    # a transposed link breaks covariance: the pin is sensitive to it
+    UT = np.swapaxes(U, 2, 3).copy()
+    UpT = np.swapaxes(Up, 2, 3).copy()
+    bad = oracle.staggered_apply(UpT, dims, nc, m, Gv)
+    badr = (g @ oracle.staggered_apply(UT, dims, nc, m, v).reshape(V, nc, 1)).reshape(-1)
+    assert np.linalg.norm(bad - badr) > 1e-3 * np.linalg.norm(badr)
+
+
+# ----------------------------------------------------------------------------
+# CG-M recurrences
+# ----------------------------------------------------------------------------
+
+def _dense_A(U, dims, nc, m):
+    n = inputs.volume(dims) * nc
+    A = np.empty((n, n), dtype=np.complex128)
+    for j in range(n):
+        A[:, j] = oracle.staggered_apply(U, dims, nc, m, _unit(n, j))
+    return A
+
+
+def test_cgm_matches_dense_solve_4x4_su3():
+    """The 4^4 SU(3) workload (768 unknowns, 8 shifts): CG-M equals LAPACK."""
+    p = inputs.lattice_4x4_su3_8shifts()
+    A = _dense_A(p.links, p.dims, p.nc, p.mass)
+    assert np.max(np.abs(A - np.conj(A.T))) < 1e-15
+    assert np.linalg.eigvalsh(A).min() > 0.9 * p.mass ** 2
+    b = p.b[0]
+    res = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, 1e-13)
+    assert res.status == 0
+    n = A.shape[0]
+    for i, s in enumerate(p.sigma):
+        xs = np.linalg.solve(A + s * np.eye(n), b)
+        assert np.linalg.norm(res.x[i] - xs) <= 1e-11 * np.linalg.norm(xs)
+    rho = oracle.true_residual_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, res.x)
+    assert np.all(rho <= 1e-12)
+
+
+def test_cgm_iterates_equal_textbook_cg():
+    """x_s after k CG-M iterations equals k iterations of textbook CG on
+    A + sigma_s (same Krylov space, same Galerkin condition)."""
+    p = inputs.lattice_4x4_su3_8shifts()
+    b = p.b[0]
+    for k in (1, 2, 3, 7, 15, 25):
+        res = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, 0.0, max_iter=k,
+                                   freeze=False)
+        assert res.iters == k
+        for i, s in enumerate(p.sigma):
+            xc, it, st = oracle.cg_staggered(p.links, p.dims, p.nc, p.mass, b, s, 0.0, max_iter=k)
+            assert it == k
+            assert np.linalg.norm(res.x[i] - xc) <= 1e-11 * np.linalg.norm(xc)
+
+
+def test_cgm_first_iteration_hand_check():
+    """After one iteration x_s = R/(P + sigma R) b, the exact shifted CG step."""
+    p = inputs.lattice_4x4_su3_8shifts()
+    b = p.b[0]
+    res = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, 0.0, max_iter=1,
+                               freeze=False)
+    R = np.vdot(b, b).real
+    P = np.vdot(b, oracle.staggered_apply(p.links, p.dims, p.nc, p.mass, b)).real
+    for i, s in enumerate(p.sigma):
+        assert np.linalg.norm(res.x[i] - R / (P + s * R) * b) <= 1e-14 * np.linalg.norm(res.x[i])
+        assert abs(res.zeta[i] - 1.0 / (1.0 + s * R / P)) <= 1e-15
+
+
+def test_cgm_collinear_residuals():
+    """b - (A + sigma_s) x_s = zeta_s r at every iteration."""
+    p = inputs.lattice_4x4_su3_8shifts()
+    b = p.b[0]
+    for k in (4, 12, 30):
+        res = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, 0.0, max_iter=k,
+                                   freeze=False)
+        for i, s in enumerate(p.sigma):
+            rs = b - oracle.staggered_apply(p.links, p.dims, p.nc, p.mass, res.x[i], sigma=s)
+            assert np.linalg.norm(rs - res.zeta[i] * res.r) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_cgm_freeze_reports_per_shift_iterations():
+    p = inputs.lattice_4x4_su3_8shifts()
+    b = p.b[0]
+    res = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, p.tol)
+    assert res.status == 0
+    # larger shifts are better conditioned and converge no later
+    assert np.all(np.diff(res.conv_iter) <= 0)
+    assert res.iters == res.conv_iter.max()
+    rho = oracle.true_residual_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, res.x)
+    assert np.all(rho <= 5 * p.tol)
+    # freezing changes nothing but the work: compare with the paper's behaviour
+    res2 = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, p.tol, freeze=False)
+    for i in range(len(p.sigma)):
+        assert np.linalg.norm(res.x[i] - res2.x[i]) <= 1e-9 * np.linalg.norm(res2.x[i])
+
+
+def test_quadratic_form_bounds():
+    """|phi|^2/(m^2+16+sigma) <= phi^dagger (A+sigma)^-1 phi <= |phi|^2/(m^2+sigma)
+    since 0 <= -D^2 <= 16 for unitary links (|D| <= 4)."""
+    p = inputs.lattice_4x4_su3_8shifts()
+    b = p.b[0]
+    res = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, 1e-12)
+    nb2 = np.vdot(b, b).real
+    for i, s in enumerate(p.sigma):
+        q = np.vdot(b, res.x[i]).real
+        assert nb2 / (p.mass ** 2 + 16 + s) <= q <= nb2 / (p.mass ** 2 + s)
+
+
+def test_zero_source_gives_zero():
+    p = inputs.lattice_4x4_su3_8shifts()
+    b = np.zeros(p.n, dtype=np.complex128)
+    res = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, b, p.sigma, p.tol)
+    assert res.status == 0 and res.iters == 0
+    assert np.all(res.x == 0)
+
+
+# ----------------------------------------------------------------------------
+# Generic block-CSR operator
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bd", [1, 2, 3])
+def test_bsr_apply_and_solve_match_dense(bd):
+    rp, ci, vals, A = inputs.random_hpd_bsr(40, bd, 4, 0.5, 21 + bd)
+    n = A.shape[0]
+    v = _vec(n, 7)
+    y = oracle.bsr_apply(rp, ci, vals, v, sigma=0.25)
+    assert np.linalg.norm(y - (A @ v + 0.25 * v)) <= 1e-13 * np.linalg.norm(y)
+    sig = inputs.log_shifts(1e-3, 2.0, 5)
+    res = oracle.cgm_bsr(rp, ci, vals, v, sig, 1e-13)
+    assert res.status == 0
+    for i, s in enumerate(sig):
+        xs = np.linalg.solve(A + s * np.eye(n), v)
+        assert np.linalg.norm(res.x[i] - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_bsr_not_hpd_is_reported():
+    rp, ci, vals, A = inputs.random_hpd_bsr(10, 2, 3, 0.5, 31)
+    neg = vals.copy()
+    for i in range(10):
+        for k in range(rp[i], rp[i + 1]):
+            if ci[k] == i:
+                neg[k] = -10.0 * np.eye(2) - np.abs(neg[k]).max() * np.eye(2) * 5
+    v = _vec(20, 8)
+    res = oracle.cgm_bsr(rp, ci, neg, v, [0.1], 1e-10, max_iter=50)
+    assert res.status in (4, 6)
+    # a matrix whose diagonal is strongly negative has v^dag A v < 0 at the
+    # first direction p = b for this v
+    Av = oracle.bsr_apply(rp, ci, neg, v)
+    if np.vdot(v, Av).real < 0:
+        assert res.status == 4
+
+
+# ----------------------------------------------------------------------------
+# Link force of S = sum_s c_s phi^dagger (A + sigma_s)^{-1} phi
+# ----------------------------------------------------------------------------
+
+def _fd_entry(U, dims, nc, m, phi, sig, c, mu, site, a, b, h, imag):
+    """Central difference of S in one link entry, written without cancellation:
+    S(U+) - S(U-) = sum_s c_s x_s+^dagger (A- - A+) x_s- for Hermitian A."""
+    Upl = U.copy(); Umi = U.copy()
+    d = (1j if imag else 1.0) * h
+    Upl[mu, site, a, b] += d
+    Umi[mu, site, a, b] -= d
+    rp = oracle.cgm_staggered(Upl, dims, nc, m, phi, sig, 1e-13)
+    rm = oracle.cgm_staggered(Umi, dims, nc, m, phi, sig, 1e-13)
+    tot = 0.0
+    for s in range(len(sig)):
+        dA = (oracle.staggered_apply(Umi, dims, nc, m, rm.x[s])
+              - oracle.staggered_apply(Upl, dims, nc, m, rm.x[s]))
+        tot += c[s] * np.vdot(rp.x[s], dA).real
+    return tot / (2 * h)
+
+
+def test_link_force_matches_central_differences():
+    dims, nc, m = (4, 4, 4, 4), 3, 0.2
+    U = inputs.su_n_links(dims, nc, 0.7, 41)
+    n = inputs.volume(dims) * nc
+    phi = _vec(n, 9)
+    sig = inputs.log_shifts(1e-2, 2.0, 4)
+    c = sig ** 0.5 / 4
+    res = oracle.cgm_staggered(U, dims, nc, m, phi, sig, 1e-13)
+    G = oracle.link_force(U, dims, nc, c, res.x)
+    g = inputs.rng(42)
+    V = inputs.volume(dims)
+    for _ in range(6):
+        mu, site = int(g.integers(4)), int(g.integers(V))
+        a, b = int(g.integers(nc)), int(g.integers(nc))
+        fre = _fd_entry(U, dims, nc, m, phi, sig, c, mu, site, a, b, 1e-6, False)
+        fim = _fd_entry(U, dims, nc, m, phi, sig, c, mu, site, a, b, 1e-6, True)
+        got = G[mu, site, a, b]
+        scale = max(abs(got), 1e-3)
+        assert abs(got.real - fre) <= 1e-6 * scale, (got, fre)
+        assert abs(got.imag - fim) <= 1e-6 * scale, (got, fim)
+
+
+def test_phi_gradient_closed_form():
+    """dS/dphi (torch convention dS/dRe + i dS/dIm) = 2 sum_s c_s x_s, checked
+    by central differences on S itself for a small lattice."""
+    dims, nc, m = (4, 4, 2, 2), 2, 0.3
+    U = inputs.su_n_links(dims, nc, 0.5, 43)
+    n = inputs.volume(dims) * nc
+    phi = _vec(n, 10)
+    sig = np.array([0.05, 0.5])
+    c = np.array([0.7, 0.3])
+    res = oracle.cgm_staggered(U, dims, nc, m, phi, sig, 1e-14)
+    grad = 2 * sum(c[s] * res.x[s] for s in range(2))
+    h = 1e-5
+    for j in (0, 7, 33):
+        for d in (1.0, 1j):
+            pp = phi.copy(); pm = phi.copy()
+            pp[j] += d * h; pm[j] -= d * h
+            sp = oracle.quad_form(pp, oracle.cgm_staggered(U, dims, nc, m, pp, sig, 1e-14).x, c)
+            sm = oracle.quad_form(pm, oracle.cgm_staggered(U, dims, nc, m, pm, sig, 1e-14).x, c)
+            fd = (sp - sm) / (2 * h)
+            want = grad[j].real if d == 1.0 else grad[j].imag
+            assert abs(fd - want) <= 1e-6 * max(1.0, abs(want))
