@@ -1,0 +1,442 @@
+"""Benchmark: multi-shift CG solve of the 24^4 SU(3) staggered operator
+exported as block-CSR (3x3 complex blocks, 331,776 block rows, 33 blocks per
+row), m = 0.05, eps = 0.8, 15 shifts log-spaced 1e-4..10, one Gaussian
+right-hand side, tolerance 1e-10 on the FP64 true residual of every shift,
+FP32 bulk with FP64 reliable updates every 50 iterations.
+
+One step = one complete solve (every shift to tolerance). Reported:
+  value      algorithmic HBM GB/s of the whole solve (bytes the executed
+             kernels must move at minimum, see `solve_bytes`) / device time;
+  e2e        the same through the C ABI with host source and solution
+             buffers (copies inside the timed region);
+  time_to_solution_ms, iterations, and the same solve in plain FP64;
+  roofline   the block-CSR SpMV kernel: algorithmic bytes per launch /
+             its mean launch time, sampled live with CUDA events on the
+             solve's stream during the timed steps;
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own replica of the workload
+(the solve does not shard); value sums the ranks' bytes over the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "multi-shift CG HBM GB/s & time-to-solution (all shifts) vs plain FP64 path"
+WORKLOAD = "24^4 SU(3) staggered A=M^dag M as block-CSR, 15 shifts 1e-4..10, 1 RHS, mixed FP32/FP64"
+L2_BYTES = 129 * 2 ** 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes
+# ----------------------------------------------------------------------------
+
+def spmv_bytes(nnzb, bd, n, real_bytes):
+    """Bytes one block-CSR SpMV must move: every block value and column index
+    once, the source vector once (neighbour reuse from cache) and the output
+    once. real_bytes = 4 (FP32) or 8 (FP64)."""
+    return nnzb * (bd * bd * 2 * real_bytes + 4) + 2 * n * 2 * real_bytes
+
+
+def solve_bytes(info, S, nnzb, bd, n, reliable_every=50):
+    """Algorithmic HBM bytes of one mixed-precision solve, from what it ran.
+
+    Multi-shift iteration k (all counts per complex unknown, FP32 = 8 B):
+      SpMV (FP32) + P;  r -= alpha Ap and |r|^2: 3 passes;
+      update: r, p read + p write (3) + per non-base shift still active
+      4 passes (x, p_s read and write; 3 in its last iteration) + base x (2).
+    Every reliable_every iterations: fold of every shift's FP32 x into FP64
+    (x32 read, x64 read+write: 40 B) and one FP64 residual SpMV
+    (+ b read, r write). True residuals: one FP64 SpMV per shift per round.
+    Refinement iteration of one shift: SpMV (FP32) + 3 + 5 passes.
+    """
+    c32 = 8
+    a32 = spmv_bytes(nnzb, bd, n, 4)
+    a64 = spmv_bytes(nnzb, bd, n, 8) + n * 16 + n * 8
+    it = int(info.iters)
+    conv = np.asarray(info.shift_iters).reshape(-1)
+    base = int(np.argmax(conv)) if len(conv) else 0
+    total = 0.0
+    for k in range(1, it + 1):
+        upd = 3
+        for s, c in enumerate(conv):
+            if s == base:
+                continue
+            cs = c if c >= 0 else it
+            if k < cs:
+                upd += 4
+            elif k == cs:
+                upd += 3
+        upd += 2
+        total += a32 + (3 + upd) * n * c32
+    chunks = -(-it // reliable_every) if it else 0
+    total += (chunks + 1) * S * 40 * n + max(chunks - 1, 0) * a64
+    rounds = int(info.refine_rounds)
+    total += (rounds + 1) * S * (a64 - n * 8)
+    ref = np.asarray(info.shift_refine_iters).reshape(-1)
+    for r_it in ref:
+        r_it = int(r_it)
+        if r_it <= 0:
+            continue
+        total += r_it * (a32 + 8 * n * c32) + a64 + 3 * n * c32
+        total += (r_it // reliable_every) * (a64 + 40 * n)
+    return total
+
+
+def fp64_solve_bytes(info, S, nnzb, bd, n):
+    """Same accounting for the plain FP64 form (16 B per complex unknown,
+    x_s updated in place, no reliable updates or folds)."""
+    c64 = 16
+    a64 = spmv_bytes(nnzb, bd, n, 8)
+    it = int(info.iters)
+    conv = np.asarray(info.shift_iters).reshape(-1)
+    base = int(np.argmax(conv)) if len(conv) else 0
+    total = 0.0
+    for k in range(1, it + 1):
+        upd = 3
+        for s, c in enumerate(conv):
+            if s == base:
+                continue
+            cs = c if c >= 0 else it
+            upd += 4 if k < cs else (3 if k == cs else 0)
+        upd += 2
+        total += a64 + (3 + upd) * n * c64
+    total += (int(info.refine_rounds) + 1) * S * (a64 + n * 16)
+    return total
+
+
+def multishift_iter_bytes_fp64(S, nnzb, bd, n):
+    """FP64 bytes of one CG-M iteration with every shift active (the oracle)."""
+    return spmv_bytes(nnzb, bd, n, 8) + (3 + 3 + 4 * (S - 1) + 2) * n * 16
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "1"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, torch):
+    if pg is not None:
+        if torch.cuda.is_available():
+            pg.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            pg.barrier()
+
+
+def reduce_max(pg, torch, v):
+    if pg is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(pg, torch, v):
+    if pg is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(problem, iters):
+    """Time `iters` CG-M iterations of the FP64 oracle on the full workload
+    (all 15 shifts active; the oracle applies A in stencil form, the same
+    matrix the block-CSR export holds). Returns (seconds, threads)."""
+    import oracle
+    t = time.perf_counter()
+    res = oracle.cgm_staggered(problem.links, problem.dims, problem.nc, problem.mass,
+                               problem.b[0], problem.sigma, 0.0, max_iter=iters, freeze=False)
+    dt = time.perf_counter() - t
+    assert res.iters == iters
+    return dt, oracle.num_threads()
+
+
+def cpu_line(problem, nnzb, bd, n, S, iters):
+    dt, cores = oracle_sample(problem, iters)
+    b = multishift_iter_bytes_fp64(S, nnzb, bd, n) * iters
+    return {"value": b / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "ms_per_iteration": 1e3 * dt / iters,
+            "sample": f"{iters} CG-M iterations (FP64, all {S} shifts active) of the full "
+                      f"24^4 workload, stencil form of the same A"}
+
+
+def run_reference(args):
+    import torch
+    world, rank, local, pg = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    from paper_1102_2143_gb300 import inputs
+    p = inputs.lattice_24x4_su3_15shifts()
+    V = inputs.volume(p.dims)
+    n, bd, nnzb, S = V * 3, 3, 33 * V, len(p.sigma)
+    iters = 4
+    for _ in range(args.warmup):
+        oracle_sample(p, 1)
+    times = []
+    cores = 1
+    for _ in range(args.steps):
+        dt, cores = oracle_sample(p, iters)
+        times.append(dt)
+    tot = sum(times)
+    b = multishift_iter_bytes_fp64(S, nnzb, bd, n) * iters * args.steps
+    val = b / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "FP64 CPU oracle, stencil form of A"},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {iters} CG-M iterations, all {S} shifts"},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1102_2143_gb300 as msc
+    from paper_1102_2143_gb300 import inputs
+
+    world, rank, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    msc.load()
+
+    p = inputs.lattice_24x4_su3_15shifts()
+    V = inputs.volume(p.dims)
+    S = len(p.sigma)
+    ctx = msc.msc_create(local, stream)
+    sop = msc.msc_op_staggered(ctx, p.nc, p.dims, torch.from_numpy(p.links).cuda(), p.mass)
+    nbr, nnzb, bd = msc.msc_op_bsr_size(sop)
+    rp = torch.empty(nbr + 1, dtype=torch.int64, device="cuda")
+    ci = torch.empty(nnzb, dtype=torch.int32, device="cuda")
+    va = torch.empty((nnzb, bd, bd), dtype=torch.complex128, device="cuda")
+    msc.msc_staggered_export_bsr(ctx, sop, rp, ci, va)
+    op = msc.msc_op_bsr(ctx, nbr, bd, rp, ci, va)
+    del va, rp, ci
+    msc.msc_op_destroy(sop)
+    n = nbr * bd
+    b_dev = torch.from_numpy(p.b[0]).cuda()
+    x_dev = torch.empty((1, S, n), dtype=torch.complex128, device="cuda")
+    b_host = torch.from_numpy(p.b[0]).pin_memory()
+    x_host = torch.empty((1, S, n), dtype=torch.complex128).pin_memory()
+
+    def step(b, x, precision=msc.MSC_MIXED):
+        x, info = msc.solve(ctx, op, b, p.sigma, x=x, tol=p.tol, precision=precision)
+        assert info.status == 0, info.status
+        return info
+
+    for _ in range(max(args.warmup, 3)):
+        step(b_dev, x_dev)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs --------------------------------
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(pg, torch)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        infos.append(step(b_dev, x_dev))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg, torch)
+    clk = clocks.stop()
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    ms = reduce_max(pg, torch, ms_local)
+    bytes_local = sum(solve_bytes(i, S, nnzb, bd, n) for i in infos) / args.steps
+    bytes_all = reduce_sum(pg, torch, bytes_local)
+    value = bytes_all / (ms * 1e-3) / 1e9
+    launches = sum(i.kernel_launches for i in infos)
+
+    # roofline of the dominant kernel (FP32 block-CSR SpMV), sampled live
+    op_ms = [i.op_ms for i in infos if i.prof_samples > 0]
+    spmv_ms = float(np.mean(op_ms)) if op_ms else None
+    spmv_b = spmv_bytes(nnzb, bd, n, 4)
+    peak, peak_kind = load_peaks()
+    roof = None
+    if spmv_ms:
+        ach = spmv_b / (spmv_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": "k_bsr<float,3,PASS_A> (SpMV + fused P)",
+                "bytes_per_launch": spmv_b, "launch_ms": spmv_ms, "peak_source": peak_kind,
+                "update_kernel_ms": float(np.mean([i.update_ms for i in infos])),
+                "rupdate_kernel_ms": float(np.mean([i.rupdate_ms for i in infos]))}
+
+    # ---- end to end: host source and solution buffers ------------------------
+    barrier(pg, torch)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    einfos = []
+    for _ in range(args.steps):
+        einfos.append(step(b_host, x_host))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg, torch)
+    e2e_ms = reduce_max(pg, torch, e0.elapsed_time(e1) / args.steps)
+    e2e_bytes = reduce_sum(pg, torch, sum(solve_bytes(i, S, nnzb, bd, n) for i in einfos) / args.steps)
+    e2e = {"value": e2e_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": S * n * 16}
+
+    # ---- plain FP64 form of the same solve -----------------------------------
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step(b_dev, x_dev, msc.MSC_FP64)
+    torch.cuda.synchronize()
+    f0.record(stream)
+    finfos = [step(b_dev, x_dev, msc.MSC_FP64) for _ in range(args.fp64_steps)]
+    f1.record(stream)
+    torch.cuda.synchronize()
+    f_ms = f0.elapsed_time(f1) / args.fp64_steps
+    fp64 = {"time_to_solution_ms": f_ms, "iterations": finfos[-1].iters,
+            "value": fp64_solve_bytes(finfos[-1], S, nnzb, bd, n) / (f_ms * 1e-3) / 1e9,
+            "unit": "GB/s", "spmv_fp64_launch_ms": finfos[-1].op_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_line(p, nnzb, bd, n, S, iters=6)
+
+    if rank == 0:
+        last = infos[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(p.dims), "nc": 3, "block_rows": nbr,
+                       "blocks": nnzb, "shifts": S, "rhs": 1, "tol": p.tol, "mass": p.mass,
+                       "eps": p.eps, "reliable_every": 50,
+                       "l2": "inputs larger than L2 (FP32 blocks %.0f MB, FP64 blocks %.0f MB)"
+                             % (nnzb * 76 / 1e6, nnzb * 148 / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "time_to_solution_ms": ms, "iterations": last.iters,
+            "refine_iterations": last.refine_iters, "refine_rounds": last.refine_rounds,
+            "iters_per_s": (last.iters + last.refine_iters) / (ms * 1e-3),
+            "max_true_rel_resid": float(np.max(last.true_rel_resid)),
+            "fp64_plain": fp64, "speedup_vs_fp64_plain": f_ms / ms,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    msc.msc_op_destroy(op)
+    msc.msc_destroy(ctx)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * msc.h - multi-shift conjugate gradient on NVIDIA GB300 (sm_103a).
+ *
+ * Solves the shifted family of eq. (linprob), Sec. 2 of Galvez & van Anders,
+ * "Accelerating the solution of families of shifted linear systems with
+ * CUDA" (arXiv:1102.2143):
+ *
+ *     (A + sigma_s I) x_s = b,   s = 0 .. S-1,
+ *
+ * for every shift from one Krylov sequence (CG-M, Algorithm 1, Sec. 2; the
+ * Krylov space is shift invariant, eq. krylov). A is Hermitian positive
+ * definite and is given either as the staggered lattice operator
+ * A = M^dagger M = m^2 - D^2 over SU(N) links, or as a generic block-CSR
+ * matrix with complex bd x bd blocks (the generic matrix the paper's solver
+ * takes, Sec. 3 and Fig. 1). The calls follow the paper's statement of the
+ * problem: operator, source, list of shifts, tolerance and iteration cap in;
+ * all x_s out in one array (Fig. 1: x holds N * N_s values).
+ *
+ * Conventions for every call:
+ *   - complex numbers are interleaved (re, im) doubles; a vector of n complex
+ *     unknowns is 2n doubles; a block is row-major;
+ *   - a data pointer may point to host memory (pageable or pinned) or to
+ *     device memory of the context's device; the library asks the CUDA
+ *     runtime which one it is and copies as needed;
+ *   - the caller owns every buffer it passes; the library copies operator
+ *     data into its own device memory at creation, so the caller may free
+ *     its arrays as soon as the call returns;
+ *   - every call returns an int status: MSC_OK (0) or one of MSC_ERR_*;
+ *     msc_strerror() names it. A context is not thread safe: calls on one
+ *     context must not overlap.
+ *   - work runs on the context's own CUDA stream, ordered after the work
+ *     already queued on the stream given at creation; calls return after
+ *     their results are in the caller's buffers.
+ */
+#ifndef MSC_H
+#define MSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MSC_OK                0
+#define MSC_ERR_ARG           1  /* invalid argument (null, size, negative shift...) */
+#define MSC_ERR_CUDA          2  /* a CUDA runtime call failed */
+#define MSC_ERR_OOM           3  /* device allocation failed */
+#define MSC_ERR_NOT_HPD       4  /* p^dagger A p <= 0 met: A is not positive definite */
+#define MSC_ERR_NONFINITE     5  /* NaN or Inf met in the source or the iteration */
+#define MSC_ERR_NOT_CONVERGED 6  /* iteration cap reached; x is written, see info */
+#define MSC_ERR_TIMEOUT       7  /* reserved: a bounded device wait gave up */
+#define MSC_ERR_UNSUPPORTED   8  /* valid request this build does not handle */
+
+/* precision of the iteration */
+#define MSC_FP64  0  /* every vector, link, block and scalar in FP64 */
+#define MSC_MIXED 1  /* FP32 operator and vector updates; FP64 zeta/alpha/beta
+                        recurrences, FP64 dot-product accumulation, FP64
+                        reliable updates of the base residual and FP64
+                        solution accumulation; each shift is then refined to
+                        the tolerance with a single-shift mixed solve */
+#define MSC_FP32  2  /* msc_op_apply only: the FP32 operator kernel */
+
+/* operator flags */
+#define MSC_LINKS_FULL  1u  /* keep all Nc*Nc FP32 link entries (no SU(N)
+                               row reconstruction), e.g. for non-unitary links */
+
+typedef struct msc_ctx msc_ctx;
+typedef struct msc_op msc_op;
+
+/* Create a context on CUDA device `device`. `cuda_stream` (a cudaStream_t,
+ * may be NULL for the legacy default stream) is the stream the caller's own
+ * work runs on; the library orders its work after it. */
+int msc_create(msc_ctx** ctx, int device, void* cuda_stream);
+int msc_destroy(msc_ctx* ctx);
+/* Change the caller stream the context orders against. */
+int msc_set_stream(msc_ctx* ctx, void* cuda_stream);
+
+/* Staggered operator A = M^dagger M = m^2 - D^2 with
+ *   D_xy = 1/2 sum_mu eta_mu(x) [U_mu(x) d_{y,x+mu} - U_mu(x-mu)^dagger d_{y,x-mu}],
+ *   eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}), periodic boundaries.
+ * nc: 2 or 3. dims[4]: extents, each even and >= 2; site index
+ * x0 + L0*(x1 + L1*(x2 + L2*x3)). links: [4][V][nc][nc] complex (FP64),
+ * U[mu][site][a][b]. A vector is [V][nc] complex. Unless MSC_LINKS_FULL is
+ * given, FP32 links keep nc-1 rows and rebuild the last one from unitarity
+ * when every link is in SU(nc) to 1e-9 (checked on the device); otherwise
+ * all entries are kept. */
+int msc_op_staggered(msc_ctx* ctx, msc_op** op, int nc, const int dims[4],
+                     const double* links, double mass, unsigned flags);
+
+/* Generic block-CSR operator: nbr block rows of complex bd x bd blocks
+ * (bd = 1, 2 or 3), row_ptr[nbr+1] (int64, non-decreasing, row_ptr[0] = 0),
+ * col_idx[nnzb] (int32 in [0, nbr)), vals[nnzb][bd][bd] complex FP64.
+ * Repeated block columns in a row add. A must be Hermitian positive
+ * definite; this is not checked here (the solve reports MSC_ERR_NOT_HPD
+ * when it meets p^dagger A p <= 0). n = nbr * bd. */
+int msc_op_bsr(msc_ctx* ctx, msc_op** op, int64_t nbr, int bd, const int64_t* row_ptr,
+               const int32_t* col_idx, const double* vals, unsigned flags);
+
+/* Export the staggered operator's A = m^2 - D^2 as block-CSR on the device:
+ * nbr = V block rows of nc x nc blocks, 33 blocks per row (the diagonal,
+ * the 8 sites two hops along one axis, the 24 sites one hop along each of
+ * two axes), row_ptr[i] = 33 i. Columns within a row are ordered by path
+ * and repeat on extents <= 4 (repeated columns add). Sizes come from
+ * msc_op_bsr_size(). Output buffers may be host or device. */
+int msc_op_bsr_size(const msc_op* staggered, int64_t* nbr, int64_t* nnzb, int* bd);
+int msc_staggered_export_bsr(msc_ctx* ctx, const msc_op* staggered, int64_t* row_ptr,
+                             int32_t* col_idx, double* vals);
+
+/* Number of complex unknowns n of an operator. */
+int msc_op_size(const msc_op* op, int64_t* n);
+
+/* recon = 1 when a staggered operator's FP32 links keep nc-1 rows and
+ * rebuild the last from unitarity, 0 otherwise (block-CSR: 0). */
+int msc_op_recon(const msc_op* op, int* recon);
+
+/* out = (A + sigma) in, with `precision` MSC_FP64 or MSC_FP32 (FP32
+ * operator kernel, FP64 in/out). in, out: [n] complex, host or device. */
+int msc_op_apply(msc_ctx* ctx, const msc_op* op, double sigma, const double* in,
+                 double* out, int precision);
+
+/* out = D in for a staggered operator (FP64). */
+int msc_op_dslash(msc_ctx* ctx, const msc_op* op, const double* in, double* out);
+
+int msc_op_destroy(msc_op* op);
+
+typedef struct {
+    double tol;          /* relative residual target per shift: |b-(A+s)x_s| <= tol |b| */
+    int max_iter;        /* cap on multi-shift iterations (and per refinement round) */
+    int precision;       /* MSC_FP64 or MSC_MIXED */
+    int reliable_every;  /* MSC_MIXED: FP64 reliable update every this many iterations */
+    int freeze_converged;/* 1: stop updating a shift once it meets tol (default);
+                            0: update every shift until all meet tol */
+    int refine;          /* max refinement rounds after the multi-shift solve
+                            (0 = none); a round re-solves each shift whose FP64
+                            true residual is above tol, warm-started from x_s */
+} msc_params;
+
+/* Fill defaults: tol 1e-10, max_iter 100000, MSC_MIXED, reliable_every 50,
+ * freeze 1, refine 4. */
+void msc_params_default(msc_params* p);
+
+typedef struct {
+    int status;             /* same as the return value of the solve */
+    int iters;              /* multi-shift iterations (max over right-hand sides) */
+    int refine_rounds;      /* refinement rounds run */
+    int refine_iters;       /* refinement iterations (sum over rounds of the
+                               max over the systems refined in that round) */
+    int reliable_updates;   /* FP64 reliable updates run (all stages) */
+    int kernel_launches;    /* kernels launched by this solve */
+    double seconds;         /* host wall time of the call */
+    /* optional caller arrays of nrhs*S entries (index rhs*S + s), or NULL */
+    int* shift_iters;       /* iteration at which shift s met tol in the
+                               multi-shift stage (-1: never) */
+    int* shift_refine_iters;/* refinement iterations spent on shift s */
+    double* true_rel_resid; /* final |b - (A+sigma_s) x_s| / |b| in FP64 */
+    /* device time per launch, sampled with CUDA events on the solve's
+       stream at the first iteration of each launch chunk of the
+       multi-shift stage in which every system was still running:
+       op_ms      the operator kernel (block-CSR SpMV with the fused P
+                  reduction; staggered: first D pass with the fused P terms),
+       rupdate_ms the residual kernel (block-CSR: r -= alpha Ap with the
+                  fused |r|^2; staggered: second D pass with r -= alpha Ap
+                  and |r|^2 fused),
+       update_ms  the fused multi-shift update kernel;
+       prof_samples the number of samples (0: not measured) */
+    double op_ms, rupdate_ms, update_ms;
+    int prof_samples;
+} msc_info;
+
+/* Solve (A + sigma_s) x_{r,s} = b_r for every shift s and right-hand side r.
+ * b: [nrhs][n] complex; sigma: [S] host array, each >= 0; x: [nrhs][S][n]
+ * complex, written for every shift (also on MSC_ERR_NOT_CONVERGED).
+ * b and x may be host or device (independently). info may be NULL.
+ * A zero b gives x = 0. */
+int msc_solve(msc_ctx* ctx, const msc_op* op, const double* b, int nrhs,
+              const double* sigma, int S, const msc_params* params, double* x,
+              msc_info* info);
+
+const char* msc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSC_H */

@@ -1,0 +1,173 @@
+// Generic block-CSR operator (the generic sparse matrix the paper's solver
+// takes, Sec. 3 and Fig. 1; A p is Algorithm 1, line 18).
+//
+// The caller's block-CSR is repacked once into sliced ELL with 32 block rows
+// per slice: inside a slice, block k of every row is stored lane-interleaved
+// ([slot][component][lane]), so that one thread per row reads its blocks and
+// a warp's loads of values and column indices are contiguous 256/128-byte
+// runs. Rows shorter than the slice's longest row are padded with zero
+// blocks pointing at column 0.
+#include "engine.h"
+
+namespace msc {
+
+template <class T> using T2 = typename C2<T>::t;
+
+__global__ void k_bsr_pack(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const double2* __restrict__ vals, int64_t nbr, int bd,
+                           const int32_t* __restrict__ slice_len,
+                           const int64_t* __restrict__ slice_start, int32_t* __restrict__ pcol,
+                           double2* __restrict__ v64, float2* __restrict__ v32, int* bad) {
+    const int e2 = bd * bd;
+    const int64_t nrow_pad = ((nbr + 31) / 32) * 32;
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < nrow_pad;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slice = row >> 5;
+        const int lane = (int)(row & 31);
+        const int len = slice_len[slice];
+        const int64_t st = slice_start[slice];
+        const int64_t b0 = row < nbr ? row_ptr[row] : 0;
+        const int64_t rl = row < nbr ? row_ptr[row + 1] - b0 : 0;
+        for (int k = 0; k < len; ++k) {
+            const int64_t slot = st + k;
+            int c = 0;
+            if (k < rl) {
+                c = col[b0 + k];
+                if (c < 0 || (int64_t)c >= nbr) { atomicExch(bad, 1); c = 0; }
+            }
+            pcol[slot * 32 + lane] = c;
+            for (int q = 0; q < e2; ++q) {
+                double2 v = {0.0, 0.0};
+                if (k < rl) v = vals[(b0 + k) * e2 + q];
+                v64[(slot * e2 + q) * 32 + lane] = v;
+                v32[(slot * e2 + q) * 32 + lane] = make_float2((float)v.x, (float)v.y);
+            }
+        }
+    }
+}
+
+cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
+                     const double2* d_vals, int* d_bad, cudaStream_t st) {
+    int64_t rows = op.nslices * 32;
+    int64_t b = (rows + 255) / 256;
+    if (b > 65535) b = 65535;
+    if (b < 1) b = 1;
+    k_bsr_pack<<<(int)b, 256, 0, st>>>(d_row_ptr, d_col, d_vals, op.nbr, op.bd, op.slice_len,
+                                        op.slice_start, op.cols, op.vals64, op.vals32, d_bad);
+    return cudaGetLastError();
+}
+
+// y = A src for one row (thread = row, lanes of a warp = rows of a slice)
+template <class T, int BD>
+__device__ __forceinline__ void bsr_row(const OpDev& A, const T2<T>* __restrict__ vals,
+                                        const T2<T>* __restrict__ src, int64_t row,
+                                        T2<T> (&y)[BD]) {
+    const int64_t slice = row >> 5;
+    const int lane = (int)(row & 31);
+    const int len = __ldg(&A.slice_len[slice]);
+    const int64_t st = __ldg(&A.slice_start[slice]);
+#pragma unroll
+    for (int a = 0; a < BD; ++a) y[a] = {T(0), T(0)};
+    const int32_t* cp = A.cols + st * 32 + lane;
+    const T2<T>* vp = vals + st * BD * BD * 32 + lane;
+#pragma unroll 3
+    for (int k = 0; k < len; ++k) {
+        const int c = __ldg(cp + (size_t)k * 32);
+        T2<T> xv[BD];
+#pragma unroll
+        for (int b = 0; b < BD; ++b) xv[b] = src[(size_t)c * BD + b];
+        const T2<T>* vk = vp + (size_t)k * BD * BD * 32;
+#pragma unroll
+        for (int a = 0; a < BD; ++a)
+#pragma unroll
+            for (int b = 0; b < BD; ++b) y[a] = cadd(y[a], cmul(__ldg(vk + (a * BD + b) * 32), xv[b]));
+    }
+}
+
+template <class T, int BD, int KIND, class TO>
+__global__ void __launch_bounds__(kThreads) k_bsr(Engine e, const PassDesc* descs, OpDev A,
+                                                  const T2<T>* __restrict__ vals) {
+    const PassDesc d = descs[blockIdx.y];
+    if (gated_off(e, d)) return;
+    const T2<T>* __restrict__ src = (const T2<T>*)d.src;
+    const T2<T>* __restrict__ aux = (const T2<T>*)d.aux;
+    const T dd = (T)d.d;
+    double local = 0.0;
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.nbr;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        T2<T> y[BD];
+        bsr_row<T, BD>(A, vals, src, row, y);
+        if (KIND == PASS_A) {  // out = (A + d) src, P term = Re src^dag out
+            T2<T>* out = (T2<T>*)d.out;
+            T loc = T(0);
+#pragma unroll
+            for (int a = 0; a < BD; ++a) {
+                const T2<T> s = src[(size_t)row * BD + a];
+                const T2<T> v = {y[a].x + dd * s.x, y[a].y + dd * s.y};
+                out[(size_t)row * BD + a] = v;
+                loc += s.x * v.x + s.y * v.y;
+            }
+            local += (double)loc;
+        } else if (KIND == PASS_C) {  // out = b - (A + d) aux, |out|^2
+            TO* out = (TO*)d.out;
+#pragma unroll
+            for (int a = 0; a < BD; ++a) {
+                const T2<T> xa = aux[(size_t)row * BD + a];
+                const double2 ba = d.b[(size_t)row * BD + a];
+                const double vx = ba.x - ((double)y[a].x + (double)dd * xa.x);
+                const double vy = ba.y - ((double)y[a].y + (double)dd * xa.y);
+                if (out) {
+                    out[2 * ((size_t)row * BD + a)] = (TO)vx;
+                    out[2 * ((size_t)row * BD + a) + 1] = (TO)vy;
+                }
+                local += vx * vx + vy * vy;
+            }
+        } else {  // PASS_D: out = (A + d) aux
+            T2<T>* out = (T2<T>*)d.out;
+#pragma unroll
+            for (int a = 0; a < BD; ++a) {
+                const T2<T> xa = aux[(size_t)row * BD + a];
+                out[(size_t)row * BD + a] = {y[a].x + dd * xa.x, y[a].y + dd * xa.y};
+            }
+        }
+    }
+    if (d.row >= 0) {
+        double tot;
+        if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
+    }
+}
+
+template <class T, int BD>
+static cudaError_t launch_bd(int kind, int out_f32, const Engine& e, const PassDesc* descs,
+                             const OpDev& A, const T2<T>* vals, dim3 grid, cudaStream_t st) {
+    switch (kind) {
+        case PASS_A: k_bsr<T, BD, PASS_A, T><<<grid, kThreads, 0, st>>>(e, descs, A, vals); break;
+        case PASS_C:
+            if (out_f32) k_bsr<T, BD, PASS_C, float><<<grid, kThreads, 0, st>>>(e, descs, A, vals);
+            else k_bsr<T, BD, PASS_C, double><<<grid, kThreads, 0, st>>>(e, descs, A, vals);
+            break;
+        case PASS_D: k_bsr<T, BD, PASS_D, T><<<grid, kThreads, 0, st>>>(e, descs, A, vals); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
+                            const PassDesc* d_descs, int npass, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, npass);
+    if (prec == PREC_F64) {
+        switch (op.bd) {
+            case 1: return launch_bd<double, 1>(kind, out_f32, e, d_descs, op, op.vals64, grid, st);
+            case 2: return launch_bd<double, 2>(kind, out_f32, e, d_descs, op, op.vals64, grid, st);
+            default: return launch_bd<double, 3>(kind, out_f32, e, d_descs, op, op.vals64, grid, st);
+        }
+    }
+    if (kind == PASS_C) return cudaErrorInvalidValue;
+    switch (op.bd) {
+        case 1: return launch_bd<float, 1>(kind, out_f32, e, d_descs, op, op.vals32, grid, st);
+        case 2: return launch_bd<float, 2>(kind, out_f32, e, d_descs, op, op.vals32, grid, st);
+        default: return launch_bd<float, 3>(kind, out_f32, e, d_descs, op, op.vals32, grid, st);
+    }
+}
+
+}  // namespace msc

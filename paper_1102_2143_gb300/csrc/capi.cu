@@ -1,0 +1,946 @@
+// C ABI of libmsc and the host driver of the multi-shift CG solve.
+//
+// The solve runs CG-M (Algorithm 1, Sec. 2) entirely on the device: the
+// host only launches CUDA graphs, each holding a chunk of iterations
+// (operator pass, residual update, fused multi-shift update per iteration),
+// and reads a few bytes of status after each chunk. In mixed precision a
+// chunk ends with an FP64 reliable update of every system's base residual.
+// After the multi-shift stage the FP64 true residual of every shift is
+// measured and each shift above the tolerance is refined by a single-shift
+// solve warm-started from its x_s.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/msc.h"
+#include "engine.h"
+
+using namespace msc;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// desc sections, each `rows` entries long
+enum { D_INIT = 0, D_K1, D_K2, D_RUA, D_RUC, D_TRA, D_TRC, D_RIA, D_RIC, D_AP1, D_AP2, D_NSECT };
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int gen = -1;
+    int kernels = 0;
+};
+
+long g_op_uid = 0;
+
+}  // namespace
+
+struct msc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t user = nullptr;
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev_sync = nullptr;
+    cudaEvent_t prof[4] = {nullptr, nullptr, nullptr, nullptr};
+    // device workspace (grow only; `gen` changes whenever a buffer moves)
+    Buf sys, slot, partial, counter, out_red, descs;
+    Buf b64, x64, t64, r, p, t, ps, xit;
+    int64_t rows_cap = 0;  // rows the desc sections were laid out for
+    int gen = 0;
+    // pinned host mirrors
+    SysScalars* h_sys = nullptr;
+    SlotScalars* h_slot = nullptr;
+    double* h_red = nullptr;
+    PassDesc* h_desc = nullptr;
+    int64_t h_rows = 0, h_slots = 0;
+    std::map<std::string, GraphEntry> graphs;
+    long launches = 0;
+};
+
+struct msc_op {
+    msc_ctx* ctx = nullptr;
+    long uid = 0;
+    OpDev dev{};
+    int64_t nnzb = 0;
+};
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_status(e_);\
+    } while (0)
+
+static int cuda_status(cudaError_t e) {
+    return e == cudaErrorMemoryAllocation ? MSC_ERR_OOM : MSC_ERR_CUDA;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static cudaError_t grow(Buf& b, size_t bytes, bool& moved) {
+    if (bytes <= b.bytes) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(b.p, 0, want);
+    if (e != cudaSuccess) return e;
+    b.bytes = want;
+    moved = true;
+    return cudaSuccess;
+}
+
+static int ensure_ws(msc_ctx* c, int64_t npad, int64_t rows, int64_t slots, int64_t rhs, size_t elem) {
+    bool moved = false;
+    rows = std::max<int64_t>(rows, 3);
+    slots = std::max<int64_t>(slots, 1);
+    rhs = std::max<int64_t>(rhs, 1);
+    if (rows > c->rows_cap) {
+        c->rows_cap = rows;
+        moved = true;
+    }
+    const int64_t R = c->rows_cap;
+    CK(grow(c->sys, sizeof(SysScalars) * R, moved));
+    CK(grow(c->slot, sizeof(SlotScalars) * std::max(slots, R), moved));
+    CK(grow(c->partial, sizeof(double) * kMaxBlocks * std::max(slots, R), moved));
+    CK(grow(c->counter, sizeof(unsigned) * std::max(slots, R), moved));
+    CK(grow(c->out_red, sizeof(double) * std::max(slots, R), moved));
+    CK(grow(c->descs, sizeof(PassDesc) * D_NSECT * R, moved));
+    CK(grow(c->b64, (size_t)rhs * npad * 16, moved));
+    CK(grow(c->x64, (size_t)slots * npad * 16, moved));
+    CK(grow(c->t64, (size_t)std::max(rows, slots) * npad * 16, moved));
+    CK(grow(c->r, (size_t)R * npad * elem, moved));
+    CK(grow(c->p, (size_t)R * npad * elem, moved));
+    CK(grow(c->t, (size_t)R * npad * elem, moved));
+    CK(grow(c->ps, (size_t)slots * npad * elem, moved));
+    CK(grow(c->xit, (size_t)slots * npad * 8, moved));
+    if (moved) c->gen++;
+    const int64_t hs = std::max(slots, R);
+    if (R > c->h_rows || hs > c->h_slots) {
+        if (c->h_sys) cudaFreeHost(c->h_sys);
+        if (c->h_slot) cudaFreeHost(c->h_slot);
+        if (c->h_red) cudaFreeHost(c->h_red);
+        if (c->h_desc) cudaFreeHost(c->h_desc);
+        CK(cudaMallocHost((void**)&c->h_sys, sizeof(SysScalars) * R));
+        CK(cudaMallocHost((void**)&c->h_slot, sizeof(SlotScalars) * hs));
+        CK(cudaMallocHost((void**)&c->h_red, sizeof(double) * hs));
+        CK(cudaMallocHost((void**)&c->h_desc, sizeof(PassDesc) * D_NSECT * R));
+        c->h_rows = R;
+        c->h_slots = hs;
+    }
+    return MSC_OK;
+}
+
+static PassDesc* dsec(msc_ctx* c, int s) { return (PassDesc*)c->descs.p + (size_t)s * c->rows_cap; }
+static PassDesc* hsec(msc_ctx* c, int s) { return c->h_desc + (size_t)s * c->rows_cap; }
+
+static cudaError_t upload_sec(msc_ctx* c, int s, int count) {
+    return cudaMemcpyAsync(dsec(c, s), hsec(c, s), sizeof(PassDesc) * count, cudaMemcpyHostToDevice,
+                           c->work);
+}
+
+static Engine engine_of(msc_ctx* c) {
+    Engine e;
+    e.sys = (SysScalars*)c->sys.p;
+    e.slot = (SlotScalars*)c->slot.p;
+    e.partial = (double*)c->partial.p;
+    e.counter = (unsigned*)c->counter.p;
+    e.out_red = (double*)c->out_red.p;
+    return e;
+}
+
+static VecSet vecs_of(msc_ctx* c, int prec, int64_t npad) {
+    VecSet v;
+    v.r = c->r.p;
+    v.p = c->p.p;
+    v.t = c->t.p;
+    v.ps = c->ps.p;
+    v.x64 = (double2*)c->x64.p;
+    v.xit = prec == PREC_F32 ? c->xit.p : c->x64.p;
+    v.b64 = (const double2*)c->b64.p;
+    v.npad = npad;
+    return v;
+}
+
+static PassDesc mkdesc(const void* src, const void* aux, const double2* b, void* out, double d,
+                       int sys, int row, int fin) {
+    PassDesc p;
+    p.src = src;
+    p.aux = aux;
+    p.b = b;
+    p.out = out;
+    p.d = d;
+    p.sys = sys;
+    p.row = row;
+    p.fin = fin;
+    p.pad = 0;
+    return p;
+}
+
+static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int out_f32, int sec,
+                           int npass) {
+    Engine e = engine_of(c);
+    const int64_t work = A.kind == OP_STAGGERED ? A.g.V : A.nbr;
+    const int nblk = grid_blocks(work, c->num_sms);
+    c->launches++;
+    if (A.kind == OP_STAGGERED)
+        return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, nblk, c->work);
+    return launch_bsr_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, nblk, c->work);
+}
+
+static int vec_blocks(msc_ctx* c, int64_t npad) { return grid_blocks(npad / 2, c->num_sms); }
+
+// One chunk of `chunk` iterations for `nsys` systems (+ reliable update).
+static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys, int chunk,
+                                 bool reliable, bool profile, int64_t npad, int& kernels) {
+    Engine e = engine_of(c);
+    VecSet v = vecs_of(c, prec, npad);
+    const int vb = vec_blocks(c, npad);
+    kernels = 0;
+    for (int it = 0; it < chunk; ++it) {
+        const bool prof = profile && it == 0;
+        if (prof) cudaEventRecordWithFlags(c->prof[0], c->work, cudaEventRecordExternal);
+        cudaError_t err = op_pass(c, A, prec, PASS_A, 0, D_K1, nsys);
+        if (err != cudaSuccess) return err;
+        if (prof) cudaEventRecordWithFlags(c->prof[1], c->work, cudaEventRecordExternal);
+        if (A.kind == OP_STAGGERED) err = op_pass(c, A, prec, PASS_B, 0, D_K2, nsys);
+        else err = launch_axpy_norm(prec, e, v, dsec(c, D_K2), nsys, vb, c->work);
+        if (err != cudaSuccess) return err;
+        if (prof) cudaEventRecordWithFlags(c->prof[2], c->work, cudaEventRecordExternal);
+        err = launch_update(prec, e, v, nsys, vb, c->work);
+        if (err != cudaSuccess) return err;
+        if (prof) cudaEventRecordWithFlags(c->prof[3], c->work, cudaEventRecordExternal);
+        kernels += 3;
+    }
+    if (reliable) {
+        cudaError_t err = launch_fold(e, v, nsys, vb, c->work);
+        if (err != cudaSuccess) return err;
+        kernels++;
+        if (A.kind == OP_STAGGERED) {
+            err = op_pass(c, A, PREC_F64, PASS_A, 0, D_RUA, nsys);
+            if (err != cudaSuccess) return err;
+            kernels++;
+        }
+        err = op_pass(c, A, PREC_F64, PASS_C, 1, D_RUC, nsys);
+        if (err != cudaSuccess) return err;
+        kernels++;
+    }
+    return cudaSuccess;
+}
+
+static int get_graph(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk, bool reliable,
+                     bool profile, int64_t npad, GraphEntry** out) {
+    char key[160];
+    snprintf(key, sizeof key, "%ld|%d|%d|%d|%d|%d|%lld", op->uid, prec, nsys, chunk, (int)reliable,
+             (int)profile, (long long)npad);
+    GraphEntry& ge = c->graphs[key];
+    if (ge.exec && ge.gen == c->gen) {
+        *out = &ge;
+        return MSC_OK;
+    }
+    if (ge.exec) {
+        cudaGraphExecDestroy(ge.exec);
+        ge.exec = nullptr;
+    }
+    long saved = c->launches;
+    CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
+    int kernels = 0;
+    cudaError_t err = enqueue_chunk(c, op->dev, prec, nsys, chunk, reliable, profile, npad, kernels);
+    cudaGraph_t g = nullptr;
+    cudaError_t err2 = cudaStreamEndCapture(c->work, &g);
+    c->launches = saved;
+    if (err != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_status(err); }
+    if (err2 != cudaSuccess) return cuda_status(err2);
+    err = cudaGraphInstantiate(&ge.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return cuda_status(err);
+    ge.gen = c->gen;
+    ge.kernels = kernels;
+    *out = &ge;
+    return MSC_OK;
+}
+
+struct ProfAcc {
+    double k1 = 0, k2 = 0, k3 = 0;
+    int n = 0;
+};
+
+// Launch chunks until every system has stopped.
+static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk, bool reliable,
+                     bool profile, int64_t npad, int max_iter, ProfAcc* pa, int* rel_updates) {
+    GraphEntry* ge = nullptr;
+    int st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, &ge);
+    if (st != MSC_OK) return st;
+    CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    const long max_chunks = (long)max_iter / chunk + 2;
+    for (long k = 0; k < max_chunks; ++k) {
+        bool any = false, all_running = true;
+        for (int j = 0; j < nsys; ++j) {
+            if (c->h_sys[j].status < ST_DONE) any = true;
+            if (c->h_sys[j].status != ST_RUNNING) all_running = false;
+        }
+        if (!any) break;
+        CK(cudaGraphLaunch(ge->exec, c->work));
+        c->launches += ge->kernels;
+        if (reliable && rel_updates) (*rel_updates)++;
+        CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost,
+                           c->work));
+        CK(cudaStreamSynchronize(c->work));
+        if (profile && pa && all_running) {
+            float a = 0, b = 0, d = 0;
+            if (cudaEventElapsedTime(&a, c->prof[0], c->prof[1]) == cudaSuccess &&
+                cudaEventElapsedTime(&b, c->prof[1], c->prof[2]) == cudaSuccess &&
+                cudaEventElapsedTime(&d, c->prof[2], c->prof[3]) == cudaSuccess) {
+                pa->k1 += a;
+                pa->k2 += b;
+                pa->k3 += d;
+                pa->n++;
+            }
+        }
+    }
+    return MSC_OK;
+}
+
+// FP64 |b_rhs - (A + sigma_s) x_s|^2 for every slot, into c->h_red.
+static int true_residuals(msc_ctx* c, const msc_op* op, int64_t npad, int nslots, int S,
+                          const double* sigma) {
+    const OpDev& A = op->dev;
+    const double dstag = A.kind == OP_STAGGERED ? A.mass * A.mass : 0.0;
+    double2* x64 = (double2*)c->x64.p;
+    double2* t64 = (double2*)c->t64.p;
+    const double2* b64 = (const double2*)c->b64.p;
+    for (int g = 0; g < nslots; ++g) {
+        const int rhs = g / S, s = g % S;
+        double2* xg = x64 + (size_t)g * npad;
+        const double2* bg = b64 + (size_t)rhs * npad;
+        if (A.kind == OP_STAGGERED) {
+            hsec(c, D_TRA)[g] = mkdesc(xg, nullptr, nullptr, t64 + (size_t)g * npad, 0.0, -1, -1, FIN_NONE);
+            hsec(c, D_TRC)[g] = mkdesc(t64 + (size_t)g * npad, xg, bg, nullptr, dstag + sigma[s], -1, g,
+                                       FIN_STORE);
+        } else {
+            hsec(c, D_TRC)[g] = mkdesc(xg, xg, bg, nullptr, sigma[s], -1, g, FIN_STORE);
+        }
+    }
+    if (A.kind == OP_STAGGERED) {
+        CK(upload_sec(c, D_TRA, nslots));
+        CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_TRA, nslots));
+    }
+    CK(upload_sec(c, D_TRC, nslots));
+    CK(op_pass(c, A, PREC_F64, PASS_C, 0, D_TRC, nslots));
+    CK(cudaMemcpyAsync(c->h_red, c->out_red.p, sizeof(double) * nslots, cudaMemcpyDeviceToHost, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    return MSC_OK;
+}
+
+static void init_sys(SysScalars& s, int S, int base, int slot0, int rhs, double d, double tol,
+                     int max_iter, int freeze) {
+    memset(&s, 0, sizeof s);
+    s.alpha_prev = 1.0;
+    s.beta_prev = 0.0;
+    s.tol2 = tol * tol;
+    s.d = d;
+    s.status = ST_RUNNING;
+    s.max_iter = max_iter;
+    s.S = S;
+    s.base = base;
+    s.slot0 = slot0;
+    s.rhs = rhs;
+    s.freeze = freeze;
+}
+
+static void init_slot(SlotScalars& q, double sigma_rel) {
+    memset(&q, 0, sizeof q);
+    q.sigma_rel = sigma_rel;
+    q.zeta = 1.0;
+    q.zeta_prev = 1.0;
+    q.zeta_new = 1.0;
+    q.active = 1;
+    q.flag = 0;
+    q.conv_iter = -1;
+}
+
+extern "C" {
+
+const char* msc_strerror(int code) {
+    switch (code) {
+        case MSC_OK: return "ok";
+        case MSC_ERR_ARG: return "invalid argument";
+        case MSC_ERR_CUDA: return "CUDA runtime error";
+        case MSC_ERR_OOM: return "out of device memory";
+        case MSC_ERR_NOT_HPD: return "operator is not Hermitian positive definite";
+        case MSC_ERR_NONFINITE: return "non-finite value in source or iteration";
+        case MSC_ERR_NOT_CONVERGED: return "iteration cap reached before tolerance";
+        case MSC_ERR_TIMEOUT: return "bounded device wait gave up";
+        case MSC_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status";
+    }
+}
+
+void msc_params_default(msc_params* p) {
+    if (!p) return;
+    p->tol = 1e-10;
+    p->max_iter = 100000;
+    p->precision = MSC_MIXED;
+    p->reliable_every = 50;
+    p->freeze_converged = 1;
+    p->refine = 4;
+}
+
+int msc_create(msc_ctx** out, int device, void* stream) {
+    if (!out) return MSC_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return MSC_ERR_ARG;
+    CK(cudaSetDevice(device));
+    msc_ctx* c = new msc_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    c->user = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sync, cudaEventDisableTiming);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->prof[i]);
+    if (e != cudaSuccess) {
+        msc_destroy(c);
+        return cuda_status(e);
+    }
+    *out = c;
+    return MSC_OK;
+}
+
+int msc_set_stream(msc_ctx* c, void* stream) {
+    if (!c) return MSC_ERR_ARG;
+    c->user = (cudaStream_t)stream;
+    return MSC_OK;
+}
+
+int msc_destroy(msc_ctx* c) {
+    if (!c) return MSC_ERR_ARG;
+    cudaSetDevice(c->device);
+    if (c->work) cudaStreamSynchronize(c->work);
+    for (auto& kv : c->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    Buf* bufs[] = {&c->sys, &c->slot, &c->partial, &c->counter, &c->out_red, &c->descs,
+                   &c->b64, &c->x64, &c->t64, &c->r, &c->p, &c->t, &c->ps, &c->xit};
+    for (Buf* b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (c->h_sys) cudaFreeHost(c->h_sys);
+    if (c->h_slot) cudaFreeHost(c->h_slot);
+    if (c->h_red) cudaFreeHost(c->h_red);
+    if (c->h_desc) cudaFreeHost(c->h_desc);
+    if (c->ev_sync) cudaEventDestroy(c->ev_sync);
+    for (int i = 0; i < 4; ++i)
+        if (c->prof[i]) cudaEventDestroy(c->prof[i]);
+    if (c->work) cudaStreamDestroy(c->work);
+    delete c;
+    return MSC_OK;
+}
+
+static void free_op_dev(OpDev& d) {
+    void* ps[] = {d.links64, d.links32, d.slice_len, d.slice_start, d.cols, d.vals64, d.vals32};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    memset(&d, 0, sizeof d);
+}
+
+int msc_op_destroy(msc_op* op) {
+    if (!op) return MSC_ERR_ARG;
+    if (op->ctx) cudaSetDevice(op->ctx->device);
+    free_op_dev(op->dev);
+    delete op;
+    return MSC_OK;
+}
+
+static int begin(msc_ctx* c) {
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventRecord(c->ev_sync, c->user));
+    CK(cudaStreamWaitEvent(c->work, c->ev_sync, 0));
+    return MSC_OK;
+}
+
+int msc_op_staggered(msc_ctx* c, msc_op** out, int nc, const int dims[4], const double* links,
+                     double mass, unsigned flags) {
+    if (!c || !out || !dims || !links) return MSC_ERR_ARG;
+    *out = nullptr;
+    if (nc != 2 && nc != 3) return MSC_ERR_ARG;
+    if (!std::isfinite(mass)) return MSC_ERR_ARG;
+    int64_t V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2 || (dims[mu] & 1)) return MSC_ERR_ARG;
+        V *= dims[mu];
+    }
+    if (V * nc > (int64_t)1 << 30) return MSC_ERR_UNSUPPORTED;
+    int st = begin(c);
+    if (st) return st;
+    msc_op* op = new msc_op();
+    op->ctx = c;
+    op->uid = ++g_op_uid;
+    OpDev& d = op->dev;
+    d.kind = OP_STAGGERED;
+    d.nc = nc;
+    for (int mu = 0; mu < 4; ++mu) d.g.L[mu] = dims[mu];
+    d.g.V = (int)V;
+    d.n = V * nc;
+    d.mass = mass;
+    const size_t nlink_bytes = (size_t)4 * V * nc * nc * 16;
+    const double2* src = (const double2*)links;
+    void* tmp = nullptr;
+    double* dmax = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](cudaError_t err) {
+        if (tmp) cudaFree(tmp);
+        if (dmax) cudaFree(dmax);
+        free_op_dev(d);
+        delete op;
+        return cuda_status(err);
+    };
+    if (!is_device_ptr(links)) {
+        e = cudaMalloc(&tmp, nlink_bytes);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, links, nlink_bytes, cudaMemcpyHostToDevice, c->work);
+        if (e != cudaSuccess) return fail(e);
+        src = (const double2*)tmp;
+    }
+    e = cudaMalloc((void**)&d.links64, nlink_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dmax, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(double), c->work);
+    if (e == cudaSuccess) e = stag_pack_links(d, src, dmax, c->work);
+    if (e == cudaSuccess) e = stag_unitarity(d, src, dmax, c->work);
+    double maxdev = 1.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&maxdev, dmax, sizeof(double), cudaMemcpyDeviceToHost, c->work);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
+    if (e != cudaSuccess) return fail(e);
+    d.recon = (!(flags & MSC_LINKS_FULL) && maxdev < 1e-9) ? 1 : 0;
+    const size_t l32 = d.recon ? (size_t)4 * V * (nc == 3 ? 3 : 1) * 16 : (size_t)4 * V * nc * nc * 8;
+    e = cudaMalloc(&d.links32, l32);
+    if (e == cudaSuccess) e = stag_pack_links32(d, src, c->work);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
+    if (e != cudaSuccess) return fail(e);
+    if (tmp) cudaFree(tmp);
+    cudaFree(dmax);
+    *out = op;
+    return MSC_OK;
+}
+
+int msc_op_bsr(msc_ctx* c, msc_op** out, int64_t nbr, int bd, const int64_t* row_ptr,
+               const int32_t* col_idx, const double* vals, unsigned flags) {
+    (void)flags;
+    if (!c || !out || !row_ptr || !col_idx || !vals) return MSC_ERR_ARG;
+    *out = nullptr;
+    if (bd < 1 || bd > 3 || nbr <= 0 || nbr > ((int64_t)1 << 31) - 1) return MSC_ERR_ARG;
+    int st = begin(c);
+    if (st) return st;
+    std::vector<int64_t> rp(nbr + 1);
+    if (is_device_ptr(row_ptr)) {
+        CK(cudaMemcpyAsync(rp.data(), row_ptr, sizeof(int64_t) * (nbr + 1), cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+    } else {
+        memcpy(rp.data(), row_ptr, sizeof(int64_t) * (nbr + 1));
+    }
+    if (rp[0] != 0) return MSC_ERR_ARG;
+    for (int64_t i = 0; i < nbr; ++i)
+        if (rp[i + 1] < rp[i]) return MSC_ERR_ARG;
+    const int64_t nnzb = rp[nbr];
+    const int64_t nslices = (nbr + 31) / 32;
+    std::vector<int32_t> slen(nslices);
+    std::vector<int64_t> sstart(nslices);
+    int64_t acc = 0;
+    for (int64_t s = 0; s < nslices; ++s) {
+        int64_t m = 0;
+        for (int64_t i = s * 32; i < std::min(nbr, s * 32 + 32); ++i) m = std::max(m, rp[i + 1] - rp[i]);
+        if (m > (1 << 30)) return MSC_ERR_ARG;
+        slen[s] = (int32_t)m;
+        sstart[s] = acc;
+        acc += m;
+    }
+    msc_op* op = new msc_op();
+    op->ctx = c;
+    op->uid = ++g_op_uid;
+    op->nnzb = nnzb;
+    OpDev& d = op->dev;
+    d.kind = OP_BSR;
+    d.bd = bd;
+    d.nbr = nbr;
+    d.n = nbr * bd;
+    d.nslices = nslices;
+    d.nslots_blk = acc;
+    void *trp = nullptr, *tcol = nullptr, *tval = nullptr;
+    int* dbad = nullptr;
+    auto fail = [&](int code) {
+        if (trp) cudaFree(trp);
+        if (tcol) cudaFree(tcol);
+        if (tval) cudaFree(tval);
+        if (dbad) cudaFree(dbad);
+        free_op_dev(d);
+        delete op;
+        return code;
+    };
+    const size_t e2 = (size_t)bd * bd;
+    cudaError_t e = cudaMalloc((void**)&d.slice_len, sizeof(int32_t) * nslices);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d.slice_start, sizeof(int64_t) * nslices);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d.cols, sizeof(int32_t) * 32 * std::max<int64_t>(acc, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d.vals64, 16 * e2 * 32 * std::max<int64_t>(acc, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d.vals32, 8 * e2 * 32 * std::max<int64_t>(acc, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&trp, sizeof(int64_t) * (nbr + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dbad, sizeof(int));
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    e = cudaMemcpyAsync(d.slice_len, slen.data(), sizeof(int32_t) * nslices, cudaMemcpyHostToDevice, c->work);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.slice_start, sstart.data(), sizeof(int64_t) * nslices, cudaMemcpyHostToDevice, c->work);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(trp, rp.data(), sizeof(int64_t) * (nbr + 1), cudaMemcpyHostToDevice, c->work);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(int), c->work);
+    const int32_t* dcol = col_idx;
+    const double2* dval = (const double2*)vals;
+    if (e == cudaSuccess && !is_device_ptr(col_idx)) {
+        e = cudaMalloc(&tcol, sizeof(int32_t) * std::max<int64_t>(nnzb, 1));
+        if (e == cudaSuccess && nnzb) e = cudaMemcpyAsync(tcol, col_idx, sizeof(int32_t) * nnzb, cudaMemcpyHostToDevice, c->work);
+        dcol = (const int32_t*)tcol;
+    }
+    if (e == cudaSuccess && !is_device_ptr(vals)) {
+        e = cudaMalloc(&tval, 16 * e2 * std::max<int64_t>(nnzb, 1));
+        if (e == cudaSuccess && nnzb) e = cudaMemcpyAsync(tval, vals, 16 * e2 * nnzb, cudaMemcpyHostToDevice, c->work);
+        dval = (const double2*)tval;
+    }
+    if (e == cudaSuccess) e = bsr_pack(d, (const int64_t*)trp, dcol, dval, dbad, c->work);
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->work);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    if (bad) return fail(MSC_ERR_ARG);
+    cudaFree(trp);
+    if (tcol) cudaFree(tcol);
+    if (tval) cudaFree(tval);
+    cudaFree(dbad);
+    *out = op;
+    return MSC_OK;
+}
+
+int msc_op_size(const msc_op* op, int64_t* n) {
+    if (!op || !n) return MSC_ERR_ARG;
+    *n = op->dev.n;
+    return MSC_OK;
+}
+
+int msc_op_recon(const msc_op* op, int* recon) {
+    if (!op || !recon) return MSC_ERR_ARG;
+    *recon = op->dev.kind == OP_STAGGERED ? op->dev.recon : 0;
+    return MSC_OK;
+}
+
+int msc_op_bsr_size(const msc_op* op, int64_t* nbr, int64_t* nnzb, int* bd) {
+    if (!op || op->dev.kind != OP_STAGGERED) return MSC_ERR_ARG;
+    if (nbr) *nbr = op->dev.g.V;
+    if (nnzb) *nnzb = (int64_t)33 * op->dev.g.V;
+    if (bd) *bd = op->dev.nc;
+    return MSC_OK;
+}
+
+int msc_staggered_export_bsr(msc_ctx* c, const msc_op* op, int64_t* row_ptr, int32_t* col_idx,
+                             double* vals) {
+    if (!c || !op || !row_ptr || !col_idx || !vals || op->dev.kind != OP_STAGGERED) return MSC_ERR_ARG;
+    int st = begin(c);
+    if (st) return st;
+    const OpDev& d = op->dev;
+    const int64_t V = d.g.V, nnzb = 33 * V;
+    const size_t vb = (size_t)nnzb * d.nc * d.nc * 16;
+    const bool drp = is_device_ptr(row_ptr), dci = is_device_ptr(col_idx), dva = is_device_ptr(vals);
+    void *trp = nullptr, *tci = nullptr, *tva = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!drp) e = cudaMalloc(&trp, sizeof(int64_t) * (V + 1));
+    if (e == cudaSuccess && !dci) e = cudaMalloc(&tci, sizeof(int32_t) * nnzb);
+    if (e == cudaSuccess && !dva) e = cudaMalloc(&tva, vb);
+    if (e == cudaSuccess)
+        e = stag_export_bsr(d, drp ? row_ptr : (int64_t*)trp, dci ? col_idx : (int32_t*)tci,
+                            dva ? (double2*)vals : (double2*)tva, c->work);
+    if (e == cudaSuccess && !drp) e = cudaMemcpyAsync(row_ptr, trp, sizeof(int64_t) * (V + 1), cudaMemcpyDeviceToHost, c->work);
+    if (e == cudaSuccess && !dci) e = cudaMemcpyAsync(col_idx, tci, sizeof(int32_t) * nnzb, cudaMemcpyDeviceToHost, c->work);
+    if (e == cudaSuccess && !dva) e = cudaMemcpyAsync(vals, tva, vb, cudaMemcpyDeviceToHost, c->work);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
+    if (trp) cudaFree(trp);
+    if (tci) cudaFree(tci);
+    if (tva) cudaFree(tva);
+    return e == cudaSuccess ? MSC_OK : cuda_status(e);
+}
+
+// out = (A + sigma) in (or D in when dslash) through the operator kernels.
+static int apply_impl(msc_ctx* c, const msc_op* op, double sigma, const double* in, double* out,
+                      int precision, bool dslash) {
+    if (!c || !op || !in || !out) return MSC_ERR_ARG;
+    if (precision != MSC_FP64 && precision != MSC_FP32) return MSC_ERR_ARG;
+    if (dslash && (op->dev.kind != OP_STAGGERED || precision != MSC_FP64)) return MSC_ERR_ARG;
+    int st = begin(c);
+    if (st) return st;
+    const OpDev& A = op->dev;
+    const int64_t n = A.n, npad = (n + 63) / 64 * 64;
+    st = ensure_ws(c, npad, 3, 1, 1, 16);
+    if (st) return st;
+    double2* t64 = (double2*)c->t64.p;
+    double2* in64 = t64;
+    double2* mid64 = t64 + npad;
+    double2* out64 = t64 + 2 * npad;
+    CK(cudaMemcpyAsync(in64, in, n * 16, cudaMemcpyDefault, c->work));
+    const double dstag = A.kind == OP_STAGGERED ? A.mass * A.mass : 0.0;
+    if (precision == MSC_FP64) {
+        if (dslash) {
+            hsec(c, D_AP1)[0] = mkdesc(in64, nullptr, nullptr, out64, 0.0, -1, -1, FIN_NONE);
+            CK(upload_sec(c, D_AP1, 1));
+            CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_AP1, 1));
+        } else if (A.kind == OP_STAGGERED) {
+            hsec(c, D_AP1)[0] = mkdesc(in64, nullptr, nullptr, mid64, 0.0, -1, -1, FIN_NONE);
+            hsec(c, D_AP2)[0] = mkdesc(mid64, in64, nullptr, out64, dstag + sigma, -1, -1, FIN_NONE);
+            CK(upload_sec(c, D_AP1, 1));
+            CK(upload_sec(c, D_AP2, 1));
+            CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_AP1, 1));
+            CK(op_pass(c, A, PREC_F64, PASS_D, 0, D_AP2, 1));
+        } else {
+            hsec(c, D_AP2)[0] = mkdesc(in64, in64, nullptr, out64, sigma, -1, -1, FIN_NONE);
+            CK(upload_sec(c, D_AP2, 1));
+            CK(op_pass(c, A, PREC_F64, PASS_D, 0, D_AP2, 1));
+        }
+    } else {
+        float2* in32 = (float2*)c->r.p;
+        float2* mid32 = (float2*)c->t.p;
+        float2* out32 = (float2*)c->p.p;
+        const int nb = grid_blocks(n, c->num_sms);
+        CK(launch_convert(in64, 0, in32, 1, n, nb, c->work));
+        if (A.kind == OP_STAGGERED) {
+            hsec(c, D_AP1)[0] = mkdesc(in32, nullptr, nullptr, mid32, 0.0, -1, -1, FIN_NONE);
+            hsec(c, D_AP2)[0] = mkdesc(mid32, in32, nullptr, out32, dstag + sigma, -1, -1, FIN_NONE);
+            CK(upload_sec(c, D_AP1, 1));
+            CK(upload_sec(c, D_AP2, 1));
+            CK(op_pass(c, A, PREC_F32, PASS_A, 0, D_AP1, 1));
+            CK(op_pass(c, A, PREC_F32, PASS_D, 0, D_AP2, 1));
+        } else {
+            hsec(c, D_AP2)[0] = mkdesc(in32, in32, nullptr, out32, sigma, -1, -1, FIN_NONE);
+            CK(upload_sec(c, D_AP2, 1));
+            CK(op_pass(c, A, PREC_F32, PASS_D, 0, D_AP2, 1));
+        }
+        CK(launch_convert(out32, 1, out64, 0, n, nb, c->work));
+    }
+    CK(cudaMemcpyAsync(out, out64, n * 16, cudaMemcpyDefault, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    return MSC_OK;
+}
+
+int msc_op_apply(msc_ctx* c, const msc_op* op, double sigma, const double* in, double* out,
+                 int precision) {
+    return apply_impl(c, op, sigma, in, out, precision, false);
+}
+
+int msc_op_dslash(msc_ctx* c, const msc_op* op, const double* in, double* out) {
+    return apply_impl(c, op, 0.0, in, out, MSC_FP64, true);
+}
+
+int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const double* sigma, int S,
+              const msc_params* prm_in, double* x, msc_info* info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || !op || !b || !x || !sigma || nrhs <= 0 || S <= 0 || S > kMaxShifts) return MSC_ERR_ARG;
+    msc_params prm;
+    msc_params_default(&prm);
+    if (prm_in) prm = *prm_in;
+    if (!(prm.tol > 0) || prm.max_iter < 0 || prm.refine < 0) return MSC_ERR_ARG;
+    if (prm.precision != MSC_FP64 && prm.precision != MSC_MIXED) return MSC_ERR_ARG;
+    if (prm.precision == MSC_MIXED && prm.reliable_every < 1) return MSC_ERR_ARG;
+    for (int s = 0; s < S; ++s)
+        if (!(sigma[s] >= 0.0) || !std::isfinite(sigma[s])) return MSC_ERR_ARG;
+    const int prec = prm.precision == MSC_MIXED ? PREC_F32 : PREC_F64;
+    const bool mixed = prec == PREC_F32;
+    int st = begin(c);
+    if (st) return st;
+    const OpDev& A = op->dev;
+    const int64_t n = A.n, npad = (n + 63) / 64 * 64;
+    const int nslots = nrhs * S;
+    const int rows = std::max(nrhs, nslots);
+    st = ensure_ws(c, npad, rows, nslots, nrhs, mixed ? 8 : 16);
+    if (st) return st;
+    const long launches0 = c->launches;
+    const size_t elem = mixed ? 8 : 16;
+    char* r = (char*)c->r.p;
+    char* p = (char*)c->p.p;
+    char* t = (char*)c->t.p;
+    double2* x64 = (double2*)c->x64.p;
+    double2* t64 = (double2*)c->t64.p;
+    double2* b64 = (double2*)c->b64.p;
+    // source in (pads cleared: the layout stride may differ from a previous solve)
+    if (npad > n) {
+        CK(cudaMemset2DAsync(b64 + n, npad * 16, 0, (npad - n) * 16, nrhs, c->work));
+        CK(cudaMemset2DAsync(t + n * elem, npad * elem, 0, (npad - n) * elem, rows, c->work));
+        CK(cudaMemset2DAsync(r + n * elem, npad * elem, 0, (npad - n) * elem, rows, c->work));
+    }
+    CK(cudaMemcpy2DAsync(b64, npad * 16, b, n * 16, n * 16, nrhs, cudaMemcpyDefault, c->work));
+    // ---- multi-shift stage ------------------------------------------------
+    int base = 0;
+    for (int s = 1; s < S; ++s)
+        if (sigma[s] < sigma[base]) base = s;
+    const double sigma0 = sigma[base];
+    const double dstag = A.kind == OP_STAGGERED ? A.mass * A.mass : 0.0;
+    const double d0 = dstag + sigma0;
+    for (int j = 0; j < nrhs; ++j) {
+        init_sys(c->h_sys[j], S, base, j * S, j, d0, prm.tol, prm.max_iter, prm.freeze_converged);
+        for (int s = 0; s < S; ++s) init_slot(c->h_slot[j * S + s], sigma[s] - sigma0);
+        const double2* bj = b64 + (size_t)j * npad;
+        double2* xb = x64 + (size_t)(j * S + base) * npad;
+        void* rj = r + (size_t)j * npad * elem;
+        void* pj = p + (size_t)j * npad * elem;
+        void* tj = t + (size_t)j * npad * elem;
+        double2* t64j = t64 + (size_t)j * npad;
+        hsec(c, D_INIT)[j] = mkdesc(nullptr, nullptr, nullptr, nullptr, 0.0, j, j, FIN_INIT);
+        if (A.kind == OP_STAGGERED) {
+            hsec(c, D_K1)[j] = mkdesc(pj, pj, nullptr, tj, d0, j, j, FIN_P);
+            hsec(c, D_K2)[j] = mkdesc(tj, pj, nullptr, rj, d0, j, j, FIN_R);
+            hsec(c, D_RUA)[j] = mkdesc(xb, nullptr, nullptr, t64j, 0.0, j, -1, FIN_NONE);
+            hsec(c, D_RUC)[j] = mkdesc(t64j, xb, bj, rj, d0, j, j, FIN_SETR);
+        } else {
+            hsec(c, D_K1)[j] = mkdesc(pj, pj, nullptr, tj, sigma0, j, j, FIN_P);
+            hsec(c, D_K2)[j] = mkdesc(nullptr, nullptr, nullptr, nullptr, 0.0, j, j, FIN_R);
+            hsec(c, D_RUC)[j] = mkdesc(xb, xb, bj, rj, sigma0, j, j, FIN_SETR);
+        }
+    }
+    CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * nrhs, cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
+    for (int s : {D_INIT, D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, s, nrhs));
+    Engine e = engine_of(c);
+    VecSet v = vecs_of(c, prec, npad);
+    const int vb = vec_blocks(c, npad);
+    CK(launch_init(prec, e, v, dsec(c, D_INIT), nrhs, vb, c->work));
+    c->launches++;
+    const int chunk = mixed ? prm.reliable_every : 25;
+    ProfAcc pa;
+    int rel = 0;
+    st = run_stage(c, op, prec, nrhs, chunk, mixed, true, npad, prm.max_iter, &pa, &rel);
+    if (st) return st;
+    int status = MSC_OK;
+    int iters = 0;
+    std::vector<double> bnorm2(nrhs);
+    for (int j = 0; j < nrhs; ++j) {
+        const SysScalars& s = c->h_sys[j];
+        iters = std::max(iters, s.it);
+        bnorm2[j] = s.bnorm2;
+        if (s.status == ST_ERR_NOT_HPD) status = MSC_ERR_NOT_HPD;
+        else if (s.status == ST_ERR_NONFINITE && status != MSC_ERR_NOT_HPD) status = MSC_ERR_NONFINITE;
+    }
+    if (mixed) {
+        CK(launch_fold(e, v, nrhs, vb, c->work));
+        c->launches++;
+    }
+    CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslots, cudaMemcpyDeviceToHost, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    std::vector<int> shift_iters(nslots), ref_iters(nslots, 0);
+    for (int g = 0; g < nslots; ++g) shift_iters[g] = c->h_slot[g].conv_iter;
+    // ---- true residuals and refinement -----------------------------------
+    std::vector<double> rho(nslots, 0.0);
+    int rounds = 0, ref_total = 0;
+    if (status == MSC_OK) {
+        st = true_residuals(c, op, npad, nslots, S, sigma);
+        if (st) return st;
+        for (int g = 0; g < nslots; ++g) {
+            const double bn2 = bnorm2[g / S];
+            rho[g] = bn2 > 0 ? std::sqrt(c->h_red[g] / bn2) : 0.0;
+        }
+        for (int round = 0; round < prm.refine; ++round) {
+            std::vector<int> todo;
+            for (int g = 0; g < nslots; ++g)
+                if (!(rho[g] <= prm.tol)) todo.push_back(g);
+            if (todo.empty()) break;
+            const int m = (int)todo.size();
+            for (int k = 0; k < m; ++k) {
+                const int g = todo[k], rhs = g / S, s = g % S;
+                const double dk = dstag + sigma[s];
+                init_sys(c->h_sys[k], 1, 0, g, rhs, dk, 0.5 * prm.tol, prm.max_iter, 1);
+                c->h_sys[k].bnorm2 = bnorm2[rhs];
+                init_slot(c->h_slot[g], 0.0);
+                const double2* bj = b64 + (size_t)rhs * npad;
+                double2* xg = x64 + (size_t)g * npad;
+                void* rk = r + (size_t)k * npad * elem;
+                void* pk = p + (size_t)k * npad * elem;
+                void* tk = t + (size_t)k * npad * elem;
+                double2* t64k = t64 + (size_t)k * npad;
+                if (A.kind == OP_STAGGERED) {
+                    hsec(c, D_RIA)[k] = mkdesc(xg, nullptr, nullptr, t64k, 0.0, k, -1, FIN_NONE);
+                    hsec(c, D_RIC)[k] = mkdesc(t64k, xg, bj, rk, dk, k, k, FIN_SETR_INIT);
+                    hsec(c, D_K1)[k] = mkdesc(pk, pk, nullptr, tk, dk, k, k, FIN_P);
+                    hsec(c, D_K2)[k] = mkdesc(tk, pk, nullptr, rk, dk, k, k, FIN_R);
+                    hsec(c, D_RUA)[k] = mkdesc(xg, nullptr, nullptr, t64k, 0.0, k, -1, FIN_NONE);
+                    hsec(c, D_RUC)[k] = mkdesc(t64k, xg, bj, rk, dk, k, k, FIN_SETR);
+                } else {
+                    hsec(c, D_RIC)[k] = mkdesc(xg, xg, bj, rk, sigma[s], k, k, FIN_SETR_INIT);
+                    hsec(c, D_K1)[k] = mkdesc(pk, pk, nullptr, tk, sigma[s], k, k, FIN_P);
+                    hsec(c, D_K2)[k] = mkdesc(nullptr, nullptr, nullptr, nullptr, 0.0, k, k, FIN_R);
+                    hsec(c, D_RUC)[k] = mkdesc(xg, xg, bj, rk, sigma[s], k, k, FIN_SETR);
+                }
+            }
+            CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * m, cudaMemcpyHostToDevice, c->work));
+            CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
+            for (int s : {D_RIA, D_RIC, D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, s, m));
+            if (A.kind == OP_STAGGERED) CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_RIA, m));
+            CK(op_pass(c, A, PREC_F64, PASS_C, mixed ? 1 : 0, D_RIC, m));
+            CK(launch_init_from_r(prec, e, v, m, vb, c->work));
+            c->launches++;
+            st = run_stage(c, op, prec, m, chunk, mixed, false, npad, prm.max_iter, nullptr, &rel);
+            if (st) return st;
+            int most = 0;
+            for (int k = 0; k < m; ++k) {
+                const SysScalars& s = c->h_sys[k];
+                ref_iters[todo[k]] += s.it;
+                most = std::max(most, s.it);
+                if (s.status == ST_ERR_NOT_HPD) status = MSC_ERR_NOT_HPD;
+                else if (s.status == ST_ERR_NONFINITE && status == MSC_OK) status = MSC_ERR_NONFINITE;
+            }
+            ref_total += most;
+            rounds++;
+            if (mixed) {
+                CK(launch_fold(e, v, m, vb, c->work));
+                c->launches++;
+            }
+            if (status != MSC_OK) break;
+            st = true_residuals(c, op, npad, nslots, S, sigma);
+            if (st) return st;
+            for (int g = 0; g < nslots; ++g) {
+                const double bn2 = bnorm2[g / S];
+                rho[g] = bn2 > 0 ? std::sqrt(c->h_red[g] / bn2) : 0.0;
+            }
+        }
+        if (status == MSC_OK) {
+            for (int g = 0; g < nslots; ++g)
+                if (!(rho[g] <= prm.tol)) status = MSC_ERR_NOT_CONVERGED;
+        }
+    }
+    // ---- solution out --------------------------------------------------------
+    CK(cudaMemcpy2DAsync(x, n * 16, x64, npad * 16, n * 16, nslots, cudaMemcpyDefault, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    if (info) {
+        info->status = status;
+        info->iters = iters;
+        info->refine_rounds = rounds;
+        info->refine_iters = ref_total;
+        info->reliable_updates = rel;
+        info->kernel_launches = (int)(c->launches - launches0);
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int g = 0; g < nslots; ++g) {
+            if (info->shift_iters) info->shift_iters[g] = shift_iters[g];
+            if (info->shift_refine_iters) info->shift_refine_iters[g] = ref_iters[g];
+            if (info->true_rel_resid) info->true_rel_resid[g] = rho[g];
+        }
+        info->op_ms = pa.n ? pa.k1 / pa.n : 0.0;
+        info->rupdate_ms = pa.n ? pa.k2 / pa.n : 0.0;
+        info->update_ms = pa.n ? pa.k3 / pa.n : 0.0;
+        info->prof_samples = pa.n;
+    }
+    return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+// Vector kernels of the multi-shift CG iteration (CG-M, Algorithm 1, Sec. 2).
+//
+// Every update in the iteration is a real scalar times a complex vector, so
+// the kernels treat a vector as a flat array of reals and move it in 16-byte
+// units (float4 = two complex FP32 values, double2 = one complex FP64 value).
+#include "engine.h"
+
+namespace msc {
+
+template <class T> struct U16;
+template <> struct U16<float> { using t = float4; static constexpr int cpu = 2; };
+template <> struct U16<double> { using t = double2; static constexpr int cpu = 1; };
+
+__device__ __forceinline__ float4 axpy(float a, float4 x, float4 y) {
+    return {fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w)};
+}
+__device__ __forceinline__ double2 axpy(double a, double2 x, double2 y) {
+    return {fma(a, x.x, y.x), fma(a, x.y, y.y)};
+}
+// a*x + b*y
+__device__ __forceinline__ float4 axpby(float a, float4 x, float b, float4 y) {
+    return {fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z), fmaf(a, x.w, b * y.w)};
+}
+__device__ __forceinline__ double2 axpby(double a, double2 x, double b, double2 y) {
+    return {fma(a, x.x, b * y.x), fma(a, x.y, b * y.y)};
+}
+__device__ __forceinline__ float sq(float4 v) { return v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w; }
+__device__ __forceinline__ double sq(double2 v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ float4 to_unit(double2 a, double2 b) {
+    return {(float)a.x, (float)a.y, (float)b.x, (float)b.y};
+}
+
+// r = b (in iteration precision), p = r, p_s = r (non-base shifts), x = 0;
+// reduction |b|^2 in FP64 from the FP64 source.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_init(Engine e, VecSet v, const PassDesc* descs) {
+    using V = typename U16<T>::t;
+    const PassDesc d = descs[blockIdx.y];
+    const int j = d.sys;
+    const SysScalars* s = &e.sys[j];
+    const int S = s->S, base = s->base, slot0 = s->slot0, rhs = s->rhs;
+    const int64_t upv = v.npad / U16<T>::cpu;
+    V* r = (V*)v.r + (size_t)j * upv;
+    V* p = (V*)v.p + (size_t)j * upv;
+    V* ps = (V*)v.ps;
+    V* xit = (V*)v.xit;
+    const double2* b = v.b64 + (size_t)rhs * v.npad;
+    double local = 0.0;
+    const V zero = {};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        V rv;
+        if constexpr (U16<T>::cpu == 2) {
+            double2 b0 = b[2 * i], b1 = b[2 * i + 1];
+            local += sq(b0) + sq(b1);
+            rv = to_unit(b0, b1);
+        } else {
+            rv = b[i];
+            local += sq(rv);
+        }
+        r[i] = rv;
+        p[i] = rv;
+        for (int k = 0; k < S; ++k) {
+            const size_t g = (size_t)(slot0 + k) * upv + i;
+            if (k != base) ps[g] = rv;
+            xit[g] = zero;
+        }
+        if constexpr (U16<T>::cpu == 2) {
+            for (int k = 0; k < S; ++k) {
+                const size_t g = (size_t)(slot0 + k) * v.npad + 2 * i;
+                v.x64[g] = {0.0, 0.0};
+                v.x64[g + 1] = {0.0, 0.0};
+            }
+        }
+    }
+    double tot;
+    if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
+}
+
+// p = r, p_s = r, x accumulator of the system's shifts = 0 (start of a solve
+// whose residual r was just computed from a warm start).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_init_from_r(Engine e, VecSet v) {
+    using V = typename U16<T>::t;
+    const int j = blockIdx.y;
+    const SysScalars* s = &e.sys[j];
+    if (load_status(s) != ST_RUNNING) return;
+    const int S = s->S, base = s->base, slot0 = s->slot0;
+    const int64_t upv = v.npad / U16<T>::cpu;
+    const V* r = (const V*)v.r + (size_t)j * upv;
+    V* p = (V*)v.p + (size_t)j * upv;
+    V* ps = (V*)v.ps;
+    V* xit = (V*)v.xit;
+    const V zero = {};
+    const bool mixed = (void*)v.xit != (void*)v.x64;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const V rv = r[i];
+        p[i] = rv;
+        for (int k = 0; k < S; ++k) {
+            const size_t g = (size_t)(slot0 + k) * upv + i;
+            if (k != base) ps[g] = rv;
+            if (mixed) xit[g] = zero;
+        }
+    }
+}
+
+// The fused multi-shift update (Algorithm 1, lines 28-29, plus p): for every
+// shift still iterating, x_s += alpha_s p_s and p_s = zeta_s' r + beta_s p_s;
+// the base shift's direction is p itself, so only its x moves; then
+// p = r + beta p. One read of r and p serves every shift.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v) {
+    using V = typename U16<T>::t;
+    const int j = blockIdx.y;
+    SysScalars* s = &e.sys[j];
+    const int st = load_status(s);
+    if (st != ST_RUNNING && st != ST_FINISHING) return;
+    __shared__ T sa[kMaxShifts], sz[kMaxShifts], sb[kMaxShifts];
+    __shared__ int sf[kMaxShifts];
+    const int S = s->S, base = s->base, slot0 = s->slot0;
+    const T beta = (T)s->beta;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        const SlotScalars* q = &e.slot[slot0 + k];
+        sf[k] = q->flag;
+        sa[k] = (T)q->alpha_s;
+        sz[k] = (T)q->zeta_new;
+        sb[k] = (T)q->beta_s;
+    }
+    __syncthreads();
+    const int64_t upv = v.npad / U16<T>::cpu;
+    const V* __restrict__ r = (const V*)v.r + (size_t)j * upv;
+    V* __restrict__ p = (V*)v.p + (size_t)j * upv;
+    V* __restrict__ ps = (V*)v.ps + (size_t)slot0 * upv;
+    V* __restrict__ xs = (V*)v.xit + (size_t)slot0 * upv;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const V ri = r[i];
+        const V pi = p[i];
+        for (int k = 0; k < S; ++k) {
+            const int f = sf[k];
+            if (f == 0) continue;
+            const size_t g = (size_t)k * upv + i;
+            if (k == base) {
+                xs[g] = axpy(sa[k], pi, xs[g]);
+                continue;
+            }
+            const V pk = ps[g];
+            xs[g] = axpy(sa[k], pk, xs[g]);
+            if (f == 2) ps[g] = axpby(sz[k], ri, sb[k], pk);
+        }
+        p[i] = axpy(beta, pi, ri);
+    }
+    if (arrive_last(e, j)) {
+        if (threadIdx.x == 0 && s->status == ST_FINISHING) s->status = ST_DONE;
+    }
+}
+
+// Block-CSR path: r -= alpha Ap and R' = |r|^2 (Algorithm 1, lines 20 and 24).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, const PassDesc* descs) {
+    using V = typename U16<T>::t;
+    const PassDesc d = descs[blockIdx.y];
+    if (gated_off(e, d)) return;
+    const int j = d.sys;
+    const T na = -(T)e.sys[j].alpha;
+    const int64_t upv = v.npad / U16<T>::cpu;
+    V* __restrict__ r = (V*)v.r + (size_t)j * upv;
+    const V* __restrict__ ap = (const V*)v.t + (size_t)j * upv;
+    double local = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const V rv = axpy(na, ap[i], r[i]);
+        r[i] = rv;
+        local += (double)sq(rv);
+    }
+    double tot;
+    if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
+}
+
+// x_s(FP64) += x_s(FP32 accumulator); accumulator = 0, for every shift of
+// the system (mixed precision; runs whatever the system's status).
+__global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v) {
+    const int j = blockIdx.y;
+    const SysScalars* s = &e.sys[j];
+    const int st = load_status(s);
+    if (st == ST_ERR_NOT_HPD || st == ST_ERR_NONFINITE) return;
+    const int S = s->S, slot0 = s->slot0;
+    const int64_t upv = v.npad / 2;
+    float4* xa = (float4*)v.xit;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < S; ++k) {
+            const size_t g = (size_t)(slot0 + k);
+            const float4 dx = xa[g * upv + i];
+            double2* x = v.x64 + g * v.npad + 2 * i;
+            double2 x0 = x[0], x1 = x[1];
+            x0.x += dx.x; x0.y += dx.y; x1.x += dx.z; x1.y += dx.w;
+            x[0] = x0;
+            x[1] = x1;
+            xa[g * upv + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+__global__ void k_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v;
+        if (src_f32) { float2 f = ((const float2*)src)[i]; v = {f.x, f.y}; }
+        else v = ((const double2*)src)[i];
+        if (dst_f32) ((float2*)dst)[i] = make_float2((float)v.x, (float)v.y);
+        else ((double2*)dst)[i] = v;
+    }
+}
+
+int grid_blocks(int64_t work, int num_sms) {
+    int64_t b = (work + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)num_sms * 8;
+    if (cap > kMaxBlocks) cap = kMaxBlocks;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_init(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
+                        int nsys, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, nsys);
+    if (prec == PREC_F32) k_init<float><<<grid, kThreads, 0, st>>>(e, v, d_descs);
+    else k_init<double><<<grid, kThreads, 0, st>>>(e, v, d_descs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int nsys, int nblk,
+                               cudaStream_t st) {
+    dim3 grid(nblk, nsys);
+    if (prec == PREC_F32) k_init_from_r<float><<<grid, kThreads, 0, st>>>(e, v);
+    else k_init_from_r<double><<<grid, kThreads, 0, st>>>(e, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, int nblk,
+                          cudaStream_t st) {
+    dim3 grid(nblk, nsys);
+    if (prec == PREC_F32) k_update<float><<<grid, kThreads, 0, st>>>(e, v);
+    else k_update<double><<<grid, kThreads, 0, st>>>(e, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
+                             int nsys, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, nsys);
+    if (prec == PREC_F32) k_axpy_norm<float><<<grid, kThreads, 0, st>>>(e, v, d_descs);
+    else k_axpy_norm<double><<<grid, kThreads, 0, st>>>(e, v, d_descs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, nsys);
+    k_fold<<<grid, kThreads, 0, st>>>(e, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n,
+                           int nblk, cudaStream_t st) {
+    k_convert<<<nblk, kThreads, 0, st>>>(src, src_f32, dst, dst_f32, n);
+    return cudaGetLastError();
+}
+
+}  // namespace msc

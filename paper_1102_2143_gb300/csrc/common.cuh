@@ -1,0 +1,305 @@
+// Shared device-side definitions of the multi-shift CG engine.
+//
+// The engine runs CG-M (Algorithm 1, Sec. 2) for `nsys` independent systems
+// that share one operator. A system has S shifts; its base shift (the
+// smallest) is the one the Krylov sequence is built on, so its direction
+// vector p_s is p itself and its zeta is exactly 1. Per-shift vectors live in
+// global "slots" g = slot0 + s.
+//
+// Recurrences, textbook convention (alpha = step, beta = direction weight;
+// the paper writes beta0 = -alpha and alpha for our beta):
+//   alpha = R / P,          P = p^dag (A + sigma0) p
+//   zeta_s' = zeta_s zeta_s^- alpha^- /
+//             (alpha beta^- (zeta_s^- - zeta_s) + zeta_s^- alpha^- (1 + (sigma_s - sigma0) alpha))
+//   alpha_s = alpha zeta_s' / zeta_s,     x_s += alpha_s p_s
+//   r -= alpha (A + sigma0) p,  R' = r^dag r,  beta = R'/R
+//   beta_s = beta (zeta_s'/zeta_s)^2,     p_s = zeta_s' r + beta_s p_s
+//   p = r + beta p
+// Shift s has met the tolerance when |zeta_s'| sqrt(R') <= tol |b|.
+//
+// The per-iteration scalar work (a few flops per shift) is done on the
+// device by the last block of the kernel that completes the reduction it
+// needs, so the host never waits inside an iteration (Sec. 3: the shift
+// constants are computed on the GPU to avoid host round trips).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace msc {
+
+constexpr int kThreads = 256;        // threads per block of every engine kernel
+constexpr int kMaxBlocks = 2048;     // partial-sum slots per reduction row
+constexpr int kMaxShifts = 128;      // shifts per system
+
+enum : int {
+    ST_RUNNING = 0,    // iterate
+    ST_FINISHING = 1,  // the current iteration is the last one
+    ST_DONE = 2,       // converged or capped
+    ST_ERR_NOT_HPD = 4,
+    ST_ERR_NONFINITE = 5,
+};
+
+// finalize actions of the last block of a reducing kernel
+enum : int {
+    FIN_NONE = 0,
+    FIN_P = 1,        // P known: alpha, zeta', alpha_s
+    FIN_R = 2,        // R' known: beta, beta_s, convergence, iteration++
+    FIN_SETR = 3,     // R := reduction (reliable update)
+    FIN_SETR_INIT = 4,// R := reduction at the start of a solve from a residual
+    FIN_INIT = 5,     // R = |b|^2 at the start of a solve from x = 0
+    FIN_STORE = 6,    // store the reduction in out_red[row]
+};
+
+struct SysScalars {
+    double R, P, alpha, alpha_prev, beta, beta_prev;
+    double bnorm2;    // |b|^2
+    double tol2;      // tol^2
+    double d;         // diagonal shift of the operator pass (m^2+sigma0 or sigma0)
+    int status, it, max_iter, capped;
+    int S, base, slot0, rhs;
+    int freeze, pad0, pad1, pad2;
+};
+
+struct SlotScalars {
+    double sigma_rel;                   // sigma_s - sigma0
+    double zeta, zeta_prev, zeta_new;
+    double alpha_s, beta_s;
+    int active;                         // still iterating
+    int flag;                           // this iteration: 0 skip, 1 x only, 2 x and p_s
+    int conv_iter;                      // iteration at which tol was met (-1)
+    int pad;
+};
+
+// One pass of an operator kernel: which vectors, which scalars, which
+// reduction. An array of these is indexed by blockIdx.y.
+struct PassDesc {
+    const void* src;    // vector the operator acts on
+    const void* aux;    // vector multiplied by d (p or x); may equal src
+    const double2* b;   // right-hand side (residual passes)
+    void* out;          // output vector (may be null for residual norms)
+    double d;           // diagonal shift
+    int sys;            // gating system (-1: always run)
+    int row;            // reduction row (-1: no reduction)
+    int fin;            // FIN_*
+    int pad;
+};
+
+struct Engine {
+    SysScalars* sys;
+    SlotScalars* slot;
+    double* partial;     // [rows][kMaxBlocks]
+    unsigned* counter;   // [rows]
+    double* out_red;     // [rows]
+};
+
+// ---------------------------------------------------------------------------
+// complex helpers (T2 = float2 or double2)
+// ---------------------------------------------------------------------------
+template <class T> struct C2;
+template <> struct C2<float> { using t = float2; };
+template <> struct C2<double> { using t = double2; };
+
+template <class T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// conj(a) * b
+template <class T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {
+    return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+}
+template <class T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return {a.x + b.x, a.y + b.y}; }
+template <class T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return {a.x - b.x, a.y - b.y}; }
+template <class T2, class T> __device__ __forceinline__ T2 cscale(T s, T2 a) { return {s * a.x, s * a.y}; }
+template <class T2> __device__ __forceinline__ T2 cconj(T2 a) { return {a.x, -a.y}; }
+
+__device__ __forceinline__ int load_status(const SysScalars* s) {
+    return __ldcg(&s->status);
+}
+
+// ---------------------------------------------------------------------------
+// block reduction + "last block finalizes" (deterministic: fixed-order sums)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the block, valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;
+}
+
+// Publishes this block's sum of v to row `row`; returns true in every thread
+// of the last block to arrive, with the fixed-order total in `total`.
+__device__ __forceinline__ bool reduce_last(const Engine& e, int row, double v, double& total) {
+    __shared__ double sh[32];
+    __shared__ int is_last;
+    __shared__ double tot;
+    double bs = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        e.partial[(size_t)row * kMaxBlocks + blockIdx.x] = bs;
+        __threadfence();
+        unsigned t = atomicAdd(&e.counter[row], 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+        acc += __ldcg(&e.partial[(size_t)row * kMaxBlocks + i]);
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        tot = s;
+        e.counter[row] = 0u;
+    }
+    __syncthreads();
+    total = tot;
+    return true;
+}
+
+// Last block only: signals that every block of a non-reducing kernel is done.
+__device__ __forceinline__ bool arrive_last(const Engine& e, int row) {
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(&e.counter[row], 1u);
+        is_last = (t == gridDim.x - 1);
+        if (is_last) e.counter[row] = 0u;
+    }
+    __syncthreads();
+    return is_last != 0;
+}
+
+// ---------------------------------------------------------------------------
+// scalar recurrences, run by the last block (all its threads)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fin_P(const Engine& e, int j, double P) {
+    SysScalars* s = &e.sys[j];
+    const double R = s->R, ap = s->alpha_prev, bp = s->beta_prev;
+    const int S = s->S, slot0 = s->slot0;
+    const bool ok = (P > 0.0) && isfinite(P) && isfinite(R);
+    const double alpha = R / P;
+    __syncthreads();
+    if (!ok) {
+        if (threadIdx.x == 0) s->status = isfinite(P) && isfinite(R) ? ST_ERR_NOT_HPD : ST_ERR_NONFINITE;
+        return;
+    }
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        SlotScalars* q = &e.slot[slot0 + k];
+        if (!q->active) { q->flag = 0; continue; }
+        const double z = q->zeta, zp = q->zeta_prev;
+        const double den = alpha * bp * (zp - z) + zp * ap * (1.0 + q->sigma_rel * alpha);
+        const double zn = z * zp * ap / den;
+        q->zeta_new = zn;
+        q->alpha_s = alpha * zn / z;
+    }
+    if (threadIdx.x == 0) { s->P = P; s->alpha = alpha; }
+}
+
+__device__ __forceinline__ void fin_R(const Engine& e, int j, double Rn) {
+    SysScalars* s = &e.sys[j];
+    const double R = s->R, alpha = s->alpha;
+    const double thr = s->tol2 * s->bnorm2;
+    const int S = s->S, slot0 = s->slot0, it = s->it, freeze = s->freeze, maxit = s->max_iter;
+    const double beta = Rn / R;
+    const bool finite = isfinite(Rn);
+    int all = 1;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        SlotScalars* q = &e.slot[slot0 + k];
+        if (!q->active) continue;
+        const double z = q->zeta, zn = q->zeta_new;
+        const double ratio = zn / z;
+        q->beta_s = beta * ratio * ratio;
+        const bool conv = (zn * zn * Rn <= thr) || !(fabs(zn) > 1e-290);
+        if (conv && q->conv_iter < 0) q->conv_iter = it + 1;
+        if (conv && freeze) { q->active = 0; q->flag = 1; }
+        else q->flag = 2;
+        q->zeta_prev = z;
+        q->zeta = zn;
+        if (q->conv_iter < 0) all = 0;
+    }
+    all = __syncthreads_and(all);
+    if (threadIdx.x == 0) {
+        s->alpha_prev = alpha;
+        s->beta_prev = beta;
+        s->beta = beta;
+        s->R = Rn;
+        s->it = it + 1;
+        if (!finite) s->status = ST_ERR_NONFINITE;
+        else if (all) s->status = ST_FINISHING;
+        else if (it + 1 >= maxit) { s->status = ST_FINISHING; s->capped = 1; }
+    }
+}
+
+// R := reduction. At the start of a solve from a residual, a system that
+// already meets the tolerance is done with nothing to iterate.
+__device__ __forceinline__ void fin_setR(const Engine& e, int j, double Rv, bool init) {
+    SysScalars* s = &e.sys[j];
+    const double thr = s->tol2 * s->bnorm2;
+    const int S = s->S, slot0 = s->slot0;
+    __syncthreads();
+    if (!isfinite(Rv)) {
+        if (threadIdx.x == 0) s->status = ST_ERR_NONFINITE;
+        return;
+    }
+    if (init && Rv <= thr) {
+        for (int k = threadIdx.x; k < S; k += blockDim.x) {
+            e.slot[slot0 + k].active = 0;
+            e.slot[slot0 + k].flag = 0;
+            e.slot[slot0 + k].conv_iter = 0;
+        }
+        if (threadIdx.x == 0) { s->R = Rv; s->status = ST_DONE; }
+        return;
+    }
+    if (threadIdx.x == 0) s->R = Rv;
+}
+
+__device__ __forceinline__ void fin_init(const Engine& e, int j, double b2) {
+    SysScalars* s = &e.sys[j];
+    const int S = s->S, slot0 = s->slot0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s->R = b2;
+        s->bnorm2 = b2;
+        if (!isfinite(b2)) s->status = ST_ERR_NONFINITE;
+        else if (b2 == 0.0) s->status = ST_DONE;
+    }
+    if (b2 == 0.0) {
+        for (int k = threadIdx.x; k < S; k += blockDim.x) {
+            e.slot[slot0 + k].active = 0;
+            e.slot[slot0 + k].conv_iter = 0;
+        }
+    }
+}
+
+__device__ __forceinline__ void finalize(const Engine& e, const PassDesc& d, double total) {
+    switch (d.fin) {
+        case FIN_P: fin_P(e, d.sys, total); break;
+        case FIN_R: fin_R(e, d.sys, total); break;
+        case FIN_SETR: fin_setR(e, d.sys, total, false); break;
+        case FIN_SETR_INIT: fin_setR(e, d.sys, total, true); break;
+        case FIN_INIT: fin_init(e, d.sys, total); break;
+        case FIN_STORE: if (threadIdx.x == 0) e.out_red[d.row] = total; break;
+        default: break;
+    }
+}
+
+// Gate at kernel entry: true if this pass has nothing to do.
+__device__ __forceinline__ bool gated_off(const Engine& e, const PassDesc& d) {
+    if (d.sys < 0) return false;
+    return load_status(&e.sys[d.sys]) != ST_RUNNING;
+}
+
+}  // namespace msc

@@ -1,0 +1,89 @@
+// Host-side declarations shared by the translation units of libmsc.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace msc {
+
+enum { PREC_F64 = 0, PREC_F32 = 1 };
+enum { OP_STAGGERED = 0, OP_BSR = 1 };
+// operator pass kinds
+enum {
+    PASS_A = 0,  // out = D src (staggered) | out = (A+d) src (BSR); reduce P terms
+    PASS_B = 1,  // staggered: r -= alpha (d aux - D src); reduce |r|^2
+    PASS_C = 2,  // out = b - (d aux - D src) | b - (A+d) src; reduce |out|^2
+    PASS_D = 3,  // out = d aux - D src | (A+d) src
+};
+
+struct StagGeom {
+    int L[4];
+    int V;
+};
+
+// Device-resident operator data.
+struct OpDev {
+    int kind;
+    int64_t n;  // complex unknowns
+    // staggered
+    int nc;
+    StagGeom g;
+    double mass;
+    int recon;          // FP32 links keep nc-1 rows
+    double2* links64;   // [4][nc*nc][V]
+    void* links32;      // full: float2 [4][nc*nc][V]; recon: float4 [4][k][V]
+    // block-CSR in sliced-ELL form, 32 rows per slice
+    int bd;
+    int64_t nbr, nslices, nslots_blk;
+    int32_t* slice_len;
+    int64_t* slice_start;
+    int32_t* cols;      // [slot][32]
+    double2* vals64;    // [slot][bd*bd][32]
+    float2* vals32;
+};
+
+// kernel launchers (return the launch error)
+cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
+                             const PassDesc* d_descs, int npass, int nblk, cudaStream_t st);
+cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
+                            const PassDesc* d_descs, int npass, int nblk, cudaStream_t st);
+
+// vector kernels; vectors are addressed as [index][npad] complex in the
+// iteration precision (prec) unless noted
+struct VecSet {
+    void* r;        // [nsys][npad]
+    void* p;        // [nsys][npad]
+    void* t;        // [nsys][npad] (t = D p or Ap)
+    void* ps;       // [slots][npad]
+    void* xit;      // [slots][npad] x accumulator in iteration precision
+    double2* x64;   // [slots][npad]
+    const double2* b64;  // [rhs][npad]
+    int64_t npad;
+};
+cudaError_t launch_init(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
+                        int nsys, int nblk, cudaStream_t st);
+cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int nsys, int nblk,
+                               cudaStream_t st);
+cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, int nblk,
+                          cudaStream_t st);
+cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
+                             int nsys, int nblk, cudaStream_t st);
+cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int nblk, cudaStream_t st);
+cudaError_t launch_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n,
+                           int nblk, cudaStream_t st);
+
+// set-up kernels
+cudaError_t stag_pack_links(OpDev& op, const double2* links_aos, double* d_maxdev,
+                            cudaStream_t st);
+cudaError_t stag_unitarity(const OpDev& op, const double2* links_aos, double* d_maxdev,
+                           cudaStream_t st);
+cudaError_t stag_pack_links32(OpDev& op, const double2* links_aos, cudaStream_t st);
+cudaError_t stag_export_bsr(const OpDev& op, int64_t* row_ptr, int32_t* col, double2* vals,
+                            cudaStream_t st);
+cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
+                     const double2* d_vals, int* d_bad, cudaStream_t st);
+
+int grid_blocks(int64_t work, int num_sms);
+
+}  // namespace msc

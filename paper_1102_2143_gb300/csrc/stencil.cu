@@ -1,0 +1,436 @@
+// Staggered operator kernels: A = M^dagger M = m^2 - D^2 with
+//   D_xy = 1/2 sum_mu eta_mu(x) [U_mu(x) d_{y,x+mu} - U_mu(x-mu)^dagger d_{y,x-mu}],
+// the lattice operator of the synthetic workload (the paper's solver is
+// operator-generic, Sec. 3; A = m^2 - D^2 follows from D^dagger = -D).
+//
+// A p is applied as two passes of D (t = D p, then Ap = (m^2+sigma0) p - D t)
+// with the CG bookkeeping fused into the passes' epilogues:
+//   pass 1 also reduces P = p^dag (A+sigma0) p = (m^2+sigma0)|p|^2 + |t|^2,
+//   pass 2 also applies r -= alpha Ap and reduces R' = |r|^2,
+// so Ap is never written to memory (Algorithm 1, lines 18-20 and 24).
+//
+// One thread handles one site. Links are stored structure-of-arrays
+// ([mu][component][site]) so that a warp's link loads are contiguous. In
+// FP32, SU(3) links keep two rows (third = conj(row0 x row1)) and SU(2)
+// links keep one row (second = (-conj u01, conj u00)).
+#include "engine.h"
+
+namespace msc {
+
+template <class T> using T2 = typename C2<T>::t;
+
+struct SiteNbrs {
+    int fwd[4], bwd[4];
+    int par[4];  // parity of x_0 + ... + x_{mu-1}
+};
+
+__device__ __forceinline__ SiteNbrs neighbours(int x, const StagGeom& g) {
+    SiteNbrs nb;
+    int c[4];
+    int rem = x;
+    c[0] = rem % g.L[0]; rem /= g.L[0];
+    c[1] = rem % g.L[1]; rem /= g.L[1];
+    c[2] = rem % g.L[2]; rem /= g.L[2];
+    c[3] = rem;
+    int stride = 1, psum = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const int L = g.L[mu];
+        nb.fwd[mu] = (c[mu] == L - 1) ? x - (L - 1) * stride : x + stride;
+        nb.bwd[mu] = (c[mu] == 0) ? x + (L - 1) * stride : x - stride;
+        nb.par[mu] = psum & 1;
+        psum += c[mu];
+        stride *= L;
+    }
+    return nb;
+}
+
+// ---------------------------------------------------------------------------
+// link loads
+// ---------------------------------------------------------------------------
+template <class T, int NC, int RECON> struct Links;
+
+// full storage: T2 [4][NC*NC][V]
+template <class T, int NC> struct Links<T, NC, 0> {
+    __device__ static __forceinline__ void load(const void* base, int mu, int x, int V,
+                                                T2<T> (&u)[NC][NC]) {
+        const T2<T>* U = (const T2<T>*)base + (size_t)mu * NC * NC * V + x;
+#pragma unroll
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) u[a][b] = U[(size_t)(a * NC + b) * V];
+    }
+};
+
+// SU(3), two rows in three float4: (u00,u01) (u02,u10) (u11,u12)
+template <> struct Links<float, 3, 1> {
+    __device__ static __forceinline__ void load(const void* base, int mu, int x, int V,
+                                                float2 (&u)[3][3]) {
+        const float4* U = (const float4*)base + (size_t)mu * 3 * V + x;
+        const float4 q0 = U[0], q1 = U[(size_t)V], q2 = U[(size_t)2 * V];
+        u[0][0] = {q0.x, q0.y}; u[0][1] = {q0.z, q0.w};
+        u[0][2] = {q1.x, q1.y}; u[1][0] = {q1.z, q1.w};
+        u[1][1] = {q2.x, q2.y}; u[1][2] = {q2.z, q2.w};
+        // row 2 = conj(row0 x row1)
+        u[2][0] = cconj(csub(cmul(u[0][1], u[1][2]), cmul(u[0][2], u[1][1])));
+        u[2][1] = cconj(csub(cmul(u[0][2], u[1][0]), cmul(u[0][0], u[1][2])));
+        u[2][2] = cconj(csub(cmul(u[0][0], u[1][1]), cmul(u[0][1], u[1][0])));
+    }
+};
+
+// SU(2), one row in one float4: (u00,u01); row 1 = (-conj u01, conj u00)
+template <> struct Links<float, 2, 1> {
+    __device__ static __forceinline__ void load(const void* base, int mu, int x, int V,
+                                                float2 (&u)[2][2]) {
+        const float4 q = ((const float4*)base)[(size_t)mu * V + x];
+        u[0][0] = {q.x, q.y};
+        u[0][1] = {q.z, q.w};
+        u[1][0] = {-q.z, q.w};
+        u[1][1] = {q.x, -q.y};
+    }
+};
+
+// y = D src at site x
+template <class T, int NC, int RECON>
+__device__ __forceinline__ void dslash_site(const void* links, const T2<T>* __restrict__ src, int x,
+                                            const StagGeom& g, T2<T> (&y)[NC]) {
+    const SiteNbrs nb = neighbours(x, g);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) y[a] = {T(0), T(0)};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        T2<T> u[NC][NC], v[NC];
+        Links<T, NC, RECON>::load(links, mu, x, g.V, u);
+#pragma unroll
+        for (int b = 0; b < NC; ++b) v[b] = src[(size_t)nb.fwd[mu] * NC + b];
+        T2<T> w[NC][NC], z[NC];
+        Links<T, NC, RECON>::load(links, mu, nb.bwd[mu], g.V, w);
+#pragma unroll
+        for (int b = 0; b < NC; ++b) z[b] = src[(size_t)nb.bwd[mu] * NC + b];
+        const T eta = nb.par[mu] ? T(-0.5) : T(0.5);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            T2<T> f = {T(0), T(0)};
+#pragma unroll
+            for (int b = 0; b < NC; ++b) {
+                f = cadd(f, cmul(u[a][b], v[b]));    // U_mu(x) src(x+mu)
+                f = csub(f, cmulc(w[b][a], z[b]));   // U_mu(x-mu)^dag src(x-mu)
+            }
+            y[a].x += eta * f.x;
+            y[a].y += eta * f.y;
+        }
+    }
+}
+
+template <class T2v> __device__ __forceinline__ double norm2d(T2v v) {
+    return (double)v.x * v.x + (double)v.y * v.y;
+}
+
+// One D pass over every site with the epilogue `KIND` (see PASS_* in engine.h).
+template <class T, int NC, int RECON, int KIND, class TO>
+__global__ void __launch_bounds__(kThreads) k_stag(Engine e, const PassDesc* descs, StagGeom g,
+                                                   const void* links) {
+    const PassDesc d = descs[blockIdx.y];
+    if (gated_off(e, d)) return;
+    const T2<T>* __restrict__ src = (const T2<T>*)d.src;
+    const T2<T>* __restrict__ aux = (const T2<T>*)d.aux;
+    const T dd = (T)d.d;
+    T alpha = T(0);
+    if (KIND == PASS_B) alpha = (T)e.sys[d.sys].alpha;
+    double local = 0.0;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.V; x += gridDim.x * blockDim.x) {
+        T2<T> y[NC];
+        dslash_site<T, NC, RECON>(links, src, x, g, y);
+        if (KIND == PASS_A) {
+            T2<T>* out = (T2<T>*)d.out;
+            T loc = T(0);
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                out[(size_t)x * NC + a] = y[a];
+                if (d.row >= 0) {
+                    const T2<T> pa = aux[(size_t)x * NC + a];
+                    loc += dd * (pa.x * pa.x + pa.y * pa.y) + y[a].x * y[a].x + y[a].y * y[a].y;
+                }
+            }
+            local += (double)loc;
+        } else if (KIND == PASS_B) {
+            T2<T>* r = (T2<T>*)d.out;
+            T loc = T(0);
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                const T2<T> pa = aux[(size_t)x * NC + a];
+                const T2<T> ap = {dd * pa.x - y[a].x, dd * pa.y - y[a].y};
+                T2<T> ra = r[(size_t)x * NC + a];
+                ra.x -= alpha * ap.x;
+                ra.y -= alpha * ap.y;
+                r[(size_t)x * NC + a] = ra;
+                loc += ra.x * ra.x + ra.y * ra.y;
+            }
+            local += (double)loc;
+        } else if (KIND == PASS_C) {
+            TO* out = (TO*)d.out;
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                const T2<T> xa = aux[(size_t)x * NC + a];
+                const double2 ba = d.b[(size_t)x * NC + a];
+                const double vx = ba.x - ((double)dd * xa.x - y[a].x);
+                const double vy = ba.y - ((double)dd * xa.y - y[a].y);
+                if (out) {
+                    out[2 * ((size_t)x * NC + a)] = (TO)vx;
+                    out[2 * ((size_t)x * NC + a) + 1] = (TO)vy;
+                }
+                local += vx * vx + vy * vy;
+            }
+        } else {  // PASS_D
+            T2<T>* out = (T2<T>*)d.out;
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                const T2<T> xa = aux[(size_t)x * NC + a];
+                out[(size_t)x * NC + a] = {dd * xa.x - y[a].x, dd * xa.y - y[a].y};
+            }
+        }
+    }
+    if (d.row >= 0) {
+        double tot;
+        if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
+    }
+}
+
+template <class T, int NC, int RECON>
+static cudaError_t launch_kind(int kind, int out_f32, const Engine& e, const PassDesc* descs,
+                               StagGeom g, const void* links, dim3 grid, cudaStream_t st) {
+    switch (kind) {
+        case PASS_A: k_stag<T, NC, RECON, PASS_A, T><<<grid, kThreads, 0, st>>>(e, descs, g, links); break;
+        case PASS_B: k_stag<T, NC, RECON, PASS_B, T><<<grid, kThreads, 0, st>>>(e, descs, g, links); break;
+        case PASS_C:
+            if (out_f32) k_stag<T, NC, RECON, PASS_C, float><<<grid, kThreads, 0, st>>>(e, descs, g, links);
+            else k_stag<T, NC, RECON, PASS_C, double><<<grid, kThreads, 0, st>>>(e, descs, g, links);
+            break;
+        default: k_stag<T, NC, RECON, PASS_D, T><<<grid, kThreads, 0, st>>>(e, descs, g, links); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
+                             const PassDesc* d_descs, int npass, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, npass);
+    if (prec == PREC_F64) {
+        if (op.nc == 3) return launch_kind<double, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links64, grid, st);
+        return launch_kind<double, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links64, grid, st);
+    }
+    if (kind == PASS_C) return cudaErrorInvalidValue;  // residual passes run in FP64
+    if (op.nc == 3) {
+        if (op.recon) return launch_kind<float, 3, 1>(kind, out_f32, e, d_descs, op.g, op.links32, grid, st);
+        return launch_kind<float, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links32, grid, st);
+    }
+    if (op.recon) return launch_kind<float, 2, 1>(kind, out_f32, e, d_descs, op.g, op.links32, grid, st);
+    return launch_kind<float, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links32, grid, st);
+}
+
+// ---------------------------------------------------------------------------
+// set-up: link packing, unitarity check, block-CSR export
+// ---------------------------------------------------------------------------
+
+// AoS [4][V][nc][nc] double2 -> SoA [4][nc*nc][V] double2
+__global__ void k_pack64(const double2* __restrict__ in, double2* __restrict__ out, int nc, int V) {
+    const int e2 = nc * nc;
+    const int64_t total = (int64_t)4 * V * e2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int comp = (int)(i % e2);
+        const int64_t ml = i / e2;
+        const int x = (int)(ml % V);
+        const int mu = (int)(ml / V);
+        out[((size_t)mu * e2 + comp) * V + x] = in[i];
+    }
+}
+
+// max over links of max(|U U^dag - 1|_max, |det U - 1|)
+__global__ void k_unitarity(const double2* __restrict__ in, int nc, int64_t nlinks,
+                            unsigned long long* maxdev) {
+    double m = 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nlinks;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const double2* u = in + l * nc * nc;
+        for (int a = 0; a < nc; ++a)
+            for (int b = 0; b < nc; ++b) {
+                double2 s = {0.0, 0.0};
+                for (int c = 0; c < nc; ++c) s = cadd(s, cmul(u[a * nc + c], cconj(u[b * nc + c])));
+                if (a == b) s.x -= 1.0;
+                m = fmax(m, fmax(fabs(s.x), fabs(s.y)));
+            }
+        double2 det;
+        if (nc == 2) {
+            det = csub(cmul(u[0], u[3]), cmul(u[1], u[2]));
+        } else {
+            det = cmul(u[0], csub(cmul(u[4], u[8]), cmul(u[5], u[7])));
+            det = csub(det, cmul(u[1], csub(cmul(u[3], u[8]), cmul(u[5], u[6]))));
+            det = cadd(det, cmul(u[2], csub(cmul(u[3], u[7]), cmul(u[4], u[6]))));
+        }
+        det.x -= 1.0;
+        m = fmax(m, fmax(fabs(det.x), fabs(det.y)));
+        if (!(m == m)) m = 1e300;
+    }
+    // non-negative doubles order like their bit patterns
+    atomicMax(maxdev, (unsigned long long)__double_as_longlong(m));
+}
+
+// FP32 links: full [4][nc*nc][V] float2, or rows [4][k][V] float4 (recon)
+__global__ void k_pack32(const double2* __restrict__ in, void* out, int nc, int V, int recon) {
+    const int e2 = nc * nc;
+    const int64_t nl = (int64_t)4 * V;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nl;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(l % V);
+        const int mu = (int)(l / V);
+        const double2* u = in + l * e2;
+        if (!recon) {
+            float2* o = (float2*)out;
+            for (int c = 0; c < e2; ++c)
+                o[((size_t)mu * e2 + c) * V + x] = make_float2((float)u[c].x, (float)u[c].y);
+        } else {
+            float4* o = (float4*)out;
+            const int k = nc == 3 ? 3 : 1;  // float4 per link: 6 or 2 complex
+            for (int q = 0; q < k; ++q)
+                o[((size_t)mu * k + q) * V + x] =
+                    make_float4((float)u[2 * q].x, (float)u[2 * q].y, (float)u[2 * q + 1].x,
+                                (float)u[2 * q + 1].y);
+        }
+    }
+}
+
+// hop matrix H(x, mu, s) of D: s=+1 -> 1/2 eta U_mu(x) (to x+mu);
+// s=-1 -> -1/2 eta U_mu(x-mu)^dag (to x-mu).
+template <int NC>
+__device__ void hop_matrix(const double2* __restrict__ U, const StagGeom& g, int x, int mu, int s,
+                           double2 (&h)[NC][NC], int& to) {
+    const SiteNbrs nb = neighbours(x, g);
+    const double eta = nb.par[mu] ? -0.5 : 0.5;
+    if (s > 0) {
+        to = nb.fwd[mu];
+        for (int a = 0; a < NC; ++a)
+            for (int b = 0; b < NC; ++b) {
+                const double2 u = U[((size_t)mu * NC * NC + a * NC + b) * g.V + x];
+                h[a][b] = {eta * u.x, eta * u.y};
+            }
+    } else {
+        to = nb.bwd[mu];
+        for (int a = 0; a < NC; ++a)
+            for (int b = 0; b < NC; ++b) {
+                const double2 u = U[((size_t)mu * NC * NC + b * NC + a) * g.V + to];
+                h[a][b] = {-eta * u.x, eta * u.y};  // -eta * conj(u)
+            }
+    }
+}
+
+template <int NC>
+__device__ void mat_acc(double2 (&acc)[NC][NC], const double2 (&a)[NC][NC], const double2 (&b)[NC][NC],
+                        double sgn) {
+    for (int i = 0; i < NC; ++i)
+        for (int j = 0; j < NC; ++j) {
+            double2 s = {0.0, 0.0};
+            for (int k = 0; k < NC; ++k) s = cadd(s, cmul(a[i][k], b[k][j]));
+            acc[i][j].x += sgn * s.x;
+            acc[i][j].y += sgn * s.y;
+        }
+}
+
+// A = m^2 - D^2 as 33 blocks per site row: slot 0 the diagonal, slots 1..8
+// two hops along one axis (1 + 2 mu + (s<0)), slots 9..32 one hop along
+// each of two axes mu < nu (9 + 4 pair + 2 (a<0) + (b<0)).
+template <int NC>
+__global__ void k_export_bsr(const double2* __restrict__ U, StagGeom g, double m2,
+                             int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+                             double2* __restrict__ vals) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.V; x += gridDim.x * blockDim.x) {
+        const int64_t r0 = (int64_t)33 * x;
+        row_ptr[x] = r0;
+        if (x == g.V - 1) row_ptr[g.V] = r0 + 33;
+        double2 blk[NC][NC];
+        double2 h1[NC][NC], h2[NC][NC];
+        int y, z;
+        // diagonal: m^2 I - sum_{mu,s} H(x,mu,s) H(x+s mu, mu, -s)
+        for (int a = 0; a < NC; ++a)
+            for (int b = 0; b < NC; ++b) blk[a][b] = {a == b ? m2 : 0.0, 0.0};
+        for (int mu = 0; mu < 4; ++mu)
+            for (int s = -1; s <= 1; s += 2) {
+                hop_matrix<NC>(U, g, x, mu, s, h1, y);
+                hop_matrix<NC>(U, g, y, mu, -s, h2, z);
+                mat_acc<NC>(blk, h1, h2, -1.0);
+            }
+        col[r0] = x;
+        for (int a = 0; a < NC; ++a)
+            for (int b = 0; b < NC; ++b) vals[(size_t)r0 * NC * NC + a * NC + b] = blk[a][b];
+        // two hops along one axis
+        for (int mu = 0; mu < 4; ++mu)
+            for (int s = -1; s <= 1; s += 2) {
+                for (int a = 0; a < NC; ++a)
+                    for (int b = 0; b < NC; ++b) blk[a][b] = {0.0, 0.0};
+                hop_matrix<NC>(U, g, x, mu, s, h1, y);
+                hop_matrix<NC>(U, g, y, mu, s, h2, z);
+                mat_acc<NC>(blk, h1, h2, -1.0);
+                const int64_t k = r0 + 1 + 2 * mu + (s < 0);
+                col[k] = z;
+                for (int a = 0; a < NC; ++a)
+                    for (int b = 0; b < NC; ++b) vals[(size_t)k * NC * NC + a * NC + b] = blk[a][b];
+            }
+        // one hop along each of two axes, both orders of the hops
+        int pair = 0;
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = mu + 1; nu < 4; ++nu, ++pair)
+                for (int sa = -1; sa <= 1; sa += 2)
+                    for (int sb = -1; sb <= 1; sb += 2) {
+                        for (int a = 0; a < NC; ++a)
+                            for (int b = 0; b < NC; ++b) blk[a][b] = {0.0, 0.0};
+                        hop_matrix<NC>(U, g, x, mu, sa, h1, y);
+                        hop_matrix<NC>(U, g, y, nu, sb, h2, z);
+                        mat_acc<NC>(blk, h1, h2, -1.0);
+                        hop_matrix<NC>(U, g, x, nu, sb, h1, y);
+                        hop_matrix<NC>(U, g, y, mu, sa, h2, z);
+                        mat_acc<NC>(blk, h1, h2, -1.0);
+                        const int64_t k = r0 + 9 + 4 * pair + 2 * (sa < 0) + (sb < 0);
+                        col[k] = z;
+                        for (int a = 0; a < NC; ++a)
+                            for (int b = 0; b < NC; ++b)
+                                vals[(size_t)k * NC * NC + a * NC + b] = blk[a][b];
+                    }
+    }
+}
+
+static int setup_blocks(int64_t work) {
+    int64_t b = (work + 255) / 256;
+    if (b > 65535) b = 65535;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t stag_pack_links(OpDev& op, const double2* links_aos, double* d_maxdev, cudaStream_t st) {
+    (void)d_maxdev;
+    const int64_t total = (int64_t)4 * op.g.V * op.nc * op.nc;
+    k_pack64<<<setup_blocks(total), 256, 0, st>>>(links_aos, op.links64, op.nc, op.g.V);
+    return cudaGetLastError();
+}
+
+cudaError_t stag_unitarity(const OpDev& op, const double2* links_aos, double* d_maxdev,
+                           cudaStream_t st) {
+    const int64_t nl = (int64_t)4 * op.g.V;
+    k_unitarity<<<setup_blocks(nl), 256, 0, st>>>(links_aos, op.nc, nl,
+                                                  (unsigned long long*)d_maxdev);
+    return cudaGetLastError();
+}
+
+cudaError_t stag_pack_links32(OpDev& op, const double2* links_aos, cudaStream_t st) {
+    const int64_t nl = (int64_t)4 * op.g.V;
+    k_pack32<<<setup_blocks(nl), 256, 0, st>>>(links_aos, op.links32, op.nc, op.g.V, op.recon);
+    return cudaGetLastError();
+}
+
+cudaError_t stag_export_bsr(const OpDev& op, int64_t* row_ptr, int32_t* col, double2* vals,
+                            cudaStream_t st) {
+    const double m2 = op.mass * op.mass;
+    if (op.nc == 3) k_export_bsr<3><<<setup_blocks(op.g.V), 128, 0, st>>>(op.links64, op.g, m2, row_ptr, col, vals);
+    else k_export_bsr<2><<<setup_blocks(op.g.V), 128, 0, st>>>(op.links64, op.g, m2, row_ptr, col, vals);
+    return cudaGetLastError();
+}
+
+}  // namespace msc
