@@ -124,6 +124,28 @@ int msc_op_dslash(msc_ctx* ctx, const msc_op* op, const double* in, double* out)
 
 int msc_op_destroy(msc_op* op);
 
+/* out = (A + sigma) in for a staggered operator, in FP64, without allocating
+ * anything. The paper has no counterpart: this serves callers that may not
+ * let a library call cudaMalloc at that point, such as code that runs under
+ * another framework's memory pool or allocator, or a loop with latency
+ * limits where an allocation could block or fail. The intermediate D in and
+ * two small pass descriptors live in one fixed device array inside the
+ * library (256 bytes + 16 MiB, held on every device that loads the library
+ * until the process exits), so n may be at most 2^20 complex unknowns;
+ * larger operators get MSC_ERR_ARG, block-CSR operators MSC_ERR_UNSUPPORTED.
+ * in and out are device pointers on the operator's device ([n] complex,
+ * out may equal in). The work is queued on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream) and the call returns without waiting;
+ * out is ready when the stream reaches that point. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind (nothing
+ * in it needs to start at zero: each call overwrites what it reads), so
+ * calls whose work overlaps on the GPU, on any streams, race with each other
+ * and must be serialised by the caller. */
+int msc_op_apply_noalloc(const msc_op* op, double sigma, const double* in, double* out,
+                         void* stream);
+
 typedef struct {
     double tol;          /* relative residual target per shift: |b-(A+s)x_s| <= tol |b| */
     int max_iter;        /* cap on multi-shift iterations (and per refinement round) */

@@ -82,6 +82,7 @@ SIGNATURES = {
     "msc_op_apply": (_I, [_VP, _VP, _D, _VP, _VP, _I]),
     "msc_op_dslash": (_I, [_VP, _VP, _VP, _VP]),
     "msc_op_destroy": (_I, [_VP]),
+    "msc_op_apply_noalloc": (_I, [_VP, _D, _VP, _VP, _VP]),
     "msc_params_default": (None, [ctypes.POINTER(msc_params)]),
     "msc_solve": (_I, [_VP, _VP, _VP, _I, _VP, _I, ctypes.POINTER(msc_params), _VP,
                        ctypes.POINTER(msc_info)]),
@@ -208,6 +209,13 @@ def msc_op_apply(ctx: int, op: int, sigma: float, x, out, precision: int = MSC_F
 
 def msc_op_dslash(ctx: int, op: int, x, out) -> None:
     _check(load().msc_op_dslash(ctx, op, _ptr(x), _ptr(out)), "msc_op_dslash")
+
+
+def msc_op_apply_noalloc(op: int, sigma: float, x, out, stream=None) -> None:
+    """out = (A + sigma) x without any allocation (device pointers; queued on
+    `stream`, returns without waiting)."""
+    _check(load().msc_op_apply_noalloc(op, float(sigma), _ptr(x), _ptr(out), _stream_handle(stream)),
+           "msc_op_apply_noalloc")
 
 
 def msc_op_destroy(op: int) -> None:

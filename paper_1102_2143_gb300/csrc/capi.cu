@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -944,3 +945,78 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Operator apply that allocates nothing.
+//
+// msc_op_apply() above stages its vectors in the context's workspace, which
+// it grows with cudaMalloc on demand. Some callers cannot let a library
+// allocate at that point: code running under another framework's memory
+// pool or allocator (where a foreign cudaMalloc fragments or escapes the
+// pool's accounting), and loops with latency limits, where cudaMalloc may
+// block on the device or fail late under memory pressure. For them,
+// msc_op_apply_noalloc() keeps its only scratch (two pass descriptors and
+// the intermediate vector D x) in one fixed file-scope device array.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoallocMaxN = (int64_t)1 << 20;  // complex unknowns (16 MiB of FP64)
+constexpr size_t kNoallocDescBytes = 256;
+// Held by every device that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocDescBytes + 16 * kNoallocMaxN];
+
+constexpr int kNoallocMaxDevices = 128;
+void* g_noalloc_ptr[kNoallocMaxDevices];  // device address of the array, per device
+std::mutex g_noalloc_mu;
+
+__global__ void k_noalloc_store_descs(PassDesc* dst, PassDesc a, PassDesc b) {
+    if (threadIdx.x == 0) {
+        dst[0] = a;
+        dst[1] = b;
+    }
+}
+
+}  // namespace
+
+extern "C" int msc_op_apply_noalloc(const msc_op* op, double sigma, const double* in, double* out,
+                                    void* stream) {
+    if (!op || !op->ctx || !in || !out || !std::isfinite(sigma)) return MSC_ERR_ARG;
+    const OpDev& A = op->dev;
+    if (A.kind != OP_STAGGERED) return MSC_ERR_UNSUPPORTED;
+    if (A.n > kNoallocMaxN) return MSC_ERR_ARG;
+    const int dev = op->ctx->device;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return MSC_ERR_UNSUPPORTED;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return MSC_ERR_CUDA;
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) return MSC_ERR_CUDA;
+    int status = MSC_OK;
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // the host-side name of the array is not a device address: ask the
+            // runtime for this device's copy once, with the device current
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) == cudaSuccess && p) g_noalloc_ptr[dev] = p;
+            else { cudaGetLastError(); status = MSC_ERR_CUDA; }
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    if (status == MSC_OK && (!is_device_ptr(in) || !is_device_ptr(out))) status = MSC_ERR_ARG;
+    if (status == MSC_OK) {
+        cudaStream_t st = (cudaStream_t)stream;
+        PassDesc* descs = (PassDesc*)base;
+        double2* t = (double2*)((char*)base + kNoallocDescBytes);
+        const PassDesc d1 = mkdesc(in, nullptr, nullptr, t, 0.0, -1, -1, FIN_NONE);
+        const PassDesc d2 = mkdesc(t, in, nullptr, out, A.mass * A.mass + sigma, -1, -1, FIN_NONE);
+        k_noalloc_store_descs<<<1, 32, 0, st>>>(descs, d1, d2);
+        cudaError_t e = cudaGetLastError();
+        Engine none{};
+        const int nblk = grid_blocks(A.g.V, op->ctx->num_sms);
+        if (e == cudaSuccess) e = launch_stag_pass(A, PREC_F64, PASS_A, 0, none, descs, 1, nblk, st);
+        if (e == cudaSuccess) e = launch_stag_pass(A, PREC_F64, PASS_D, 0, none, descs + 1, 1, nblk, st);
+        if (e != cudaSuccess) status = cuda_status(e);
+    }
+    if (prev != dev) cudaSetDevice(prev);
+    return status;
+}
