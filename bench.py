@@ -59,71 +59,62 @@ def spmv_bytes(nnzb, bd, n, real_bytes):
     return nnzb * (bd * bd * 2 * real_bytes + 4) + 2 * n * 2 * real_bytes
 
 
-def solve_bytes(info, S, nnzb, bd, n, reliable_every=50):
-    """Algorithmic HBM bytes of one mixed-precision solve, from what it ran.
+def solve_bytes(info, S, nnzb, bd, n, mixed=True, reliable_every=50, group=8):
+    """Algorithmic HBM bytes of one solve, from what it ran.
 
-    Multi-shift iteration k (all counts per complex unknown, FP32 = 8 B):
-      SpMV (FP32) + P;  r -= alpha Ap and |r|^2: 3 passes;
-      update: r, p read + p write (3) + per non-base shift still active
-      4 passes (x, p_s read and write; 3 in its last iteration) + base x (2).
-    Every reliable_every iterations: fold of every shift's FP32 x into FP64
-    (x32 read, x64 read+write: 40 B) and one FP64 residual SpMV
-    (+ b read, r write). True residuals: one FP64 SpMV per shift per round.
-    Refinement iteration of one shift: SpMV (FP32) + 3 + 5 passes.
+    c = bytes of one complex unknown in the iteration precision (8 mixed,
+    16 FP64); "passes" below are reads or writes of one vector.
+    Multi-shift iteration k:
+      SpMV: every block value and column index once, source and output once;
+      r -= alpha Ap with |r|^2: 3 passes;
+      update: r, p read + p write (3), every non-base shift still active
+      4 passes (3 in its last iteration), the base shift's x 2 passes.
+    Mixed only: at every chunk end (reliable_every iterations) a fold of
+      each shift's FP32 x into FP64 (x32 read, x64 read+write = 40 B per
+      unknown) and, while running, one FP64 residual SpMV (+ b read, r write).
+    Checks: each check round applies the FP64 operator to every shift it
+      checks (round 0: all S; later rounds: the shifts just refined).
+    Refinement iteration k: the SpMV reads the matrix once per group of
+      `group` refined shifts with one still iterating, plus source and output
+      per iterating shift; r update 3 passes and update 5 passes per shift;
+      mixed: reliable update and fold every reliable_every iterations.
     """
-    c32 = 8
-    a32 = spmv_bytes(nnzb, bd, n, 4)
-    a64 = spmv_bytes(nnzb, bd, n, 8) + n * 16 + n * 8
+    rb = 4 if mixed else 8
+    c = 2 * rb
+    mat = nnzb * (bd * bd * 2 * rb + 4)
+    a_it = mat + 2 * n * c
+    a64 = spmv_bytes(nnzb, bd, n, 8) + n * 16 + n * c
     it = int(info.iters)
     conv = np.asarray(info.shift_iters).reshape(-1)
     base = int(np.argmax(conv)) if len(conv) else 0
     total = 0.0
     for k in range(1, it + 1):
-        upd = 3
-        for s, c in enumerate(conv):
+        upd = 3 + 2
+        for s, cv in enumerate(conv):
             if s == base:
                 continue
-            cs = c if c >= 0 else it
-            if k < cs:
-                upd += 4
-            elif k == cs:
-                upd += 3
-        upd += 2
-        total += a32 + (3 + upd) * n * c32
-    chunks = -(-it // reliable_every) if it else 0
-    total += (chunks + 1) * S * 40 * n + max(chunks - 1, 0) * a64
-    rounds = int(info.refine_rounds)
-    total += (rounds + 1) * S * (a64 - n * 8)
+            cs = cv if cv >= 0 else it
+            upd += 4 if k < cs else (3 if k == cs else 0)
+        total += a_it + (3 + upd) * n * c
+    if mixed:
+        chunks = -(-it // reliable_every) if it else 0
+        total += (chunks + 1) * S * 40 * n + max(chunks - 1, 0) * a64
     ref = np.asarray(info.shift_refine_iters).reshape(-1)
-    for r_it in ref:
-        r_it = int(r_it)
-        if r_it <= 0:
-            continue
-        total += r_it * (a32 + 8 * n * c32) + a64 + 3 * n * c32
-        total += (r_it // reliable_every) * (a64 + 40 * n)
+    refined = int(np.count_nonzero(ref))
+    total += (S + refined * int(info.refine_rounds)) * a64
+    kmax = int(ref.max()) if len(ref) else 0
+    for k in range(1, kmax + 1):
+        act = [s for s in range(len(ref)) if ref[s] >= k]
+        groups = len({s // group for s in act})
+        total += groups * mat + len(act) * (2 + 3 + 5) * n * c
+        if mixed and k % reliable_every == 0:
+            total += len(act) * (a64 + 40 * n)
     return total
 
 
 def fp64_solve_bytes(info, S, nnzb, bd, n):
-    """Same accounting for the plain FP64 form (16 B per complex unknown,
-    x_s updated in place, no reliable updates or folds)."""
-    c64 = 16
-    a64 = spmv_bytes(nnzb, bd, n, 8)
-    it = int(info.iters)
-    conv = np.asarray(info.shift_iters).reshape(-1)
-    base = int(np.argmax(conv)) if len(conv) else 0
-    total = 0.0
-    for k in range(1, it + 1):
-        upd = 3
-        for s, c in enumerate(conv):
-            if s == base:
-                continue
-            cs = c if c >= 0 else it
-            upd += 4 if k < cs else (3 if k == cs else 0)
-        upd += 2
-        total += a64 + (3 + upd) * n * c64
-    total += (int(info.refine_rounds) + 1) * S * (a64 + n * 16)
-    return total
+    """The plain FP64 form (16 B per complex unknown, x_s updated in place)."""
+    return solve_bytes(info, S, nnzb, bd, n, mixed=False)
 
 
 def multishift_iter_bytes_fp64(S, nnzb, bd, n):

@@ -80,7 +80,7 @@ __device__ __forceinline__ void bsr_row(const OpDev& A, const T2<T>* __restrict_
 #pragma unroll
         for (int a = 0; a < BD; ++a)
 #pragma unroll
-            for (int b = 0; b < BD; ++b) y[a] = cadd(y[a], cmul(__ldg(vk + (a * BD + b) * 32), xv[b]));
+            for (int b = 0; b < BD; ++b) cfma(y[a], __ldg(vk + (a * BD + b) * 32), xv[b]);
     }
 }
 
@@ -137,36 +137,144 @@ __global__ void __launch_bounds__(kThreads) k_bsr(Engine e, const PassDesc* desc
     }
 }
 
+// y_j = (A + d_j) src_j for up to G systems j sharing the matrix: each block
+// value and column index is read once and applied to every system of the
+// group (the refinement stage and several right-hand sides). Epilogue as
+// PASS_A, with one P reduction per system.
+template <class T, int BD, int G>
+__global__ void __launch_bounds__(kThreads, 2) k_bsr_multi(Engine e, const PassDesc* descs, int npass,
+                                                           OpDev A, const T2<T>* __restrict__ vals) {
+    __shared__ PassDesc sd[G];
+    __shared__ unsigned s_mask;
+    if (threadIdx.x == 0) s_mask = 0u;
+    __syncthreads();
+    if (threadIdx.x < G) {
+        const int j = blockIdx.y * G + threadIdx.x;
+        if (j < npass) {
+            sd[threadIdx.x] = descs[j];
+            if (!gated_off(e, sd[threadIdx.x])) atomicOr(&s_mask, 1u << threadIdx.x);
+        }
+    }
+    __syncthreads();
+    const unsigned mask = s_mask;
+    if (!mask) return;
+    double local[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) local[g] = 0.0;
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.nbr;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slice = row >> 5;
+        const int lane = (int)(row & 31);
+        const int len = __ldg(&A.slice_len[slice]);
+        const int64_t st = __ldg(&A.slice_start[slice]);
+        T2<T> acc[G][BD];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int a = 0; a < BD; ++a) acc[g][a] = {T(0), T(0)};
+        const int32_t* cp = A.cols + st * 32 + lane;
+        const T2<T>* vp = vals + st * BD * BD * 32 + lane;
+#pragma unroll 2
+        for (int k = 0; k < len; ++k) {
+            const int c = __ldg(cp + (size_t)k * 32);
+            const T2<T>* vk = vp + (size_t)k * BD * BD * 32;
+            T2<T> v[BD][BD];
+#pragma unroll
+            for (int a = 0; a < BD; ++a)
+#pragma unroll
+                for (int b = 0; b < BD; ++b) v[a][b] = __ldg(vk + (a * BD + b) * 32);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (!((mask >> g) & 1u)) continue;
+                const T2<T>* src = (const T2<T>*)sd[g].src;
+                T2<T> xv[BD];
+#pragma unroll
+                for (int b = 0; b < BD; ++b) xv[b] = src[(size_t)c * BD + b];
+#pragma unroll
+                for (int a = 0; a < BD; ++a)
+#pragma unroll
+                    for (int b = 0; b < BD; ++b) cfma(acc[g][a], v[a][b], xv[b]);
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (!((mask >> g) & 1u)) continue;
+            const T2<T>* src = (const T2<T>*)sd[g].src;
+            T2<T>* out = (T2<T>*)sd[g].out;
+            const T dd = (T)sd[g].d;
+            T loc = T(0);
+#pragma unroll
+            for (int a = 0; a < BD; ++a) {
+                const T2<T> s = src[(size_t)row * BD + a];
+                const T2<T> y = {acc[g][a].x + dd * s.x, acc[g][a].y + dd * s.y};
+                out[(size_t)row * BD + a] = y;
+                loc += s.x * y.x + s.y * y.y;
+            }
+            local[g] += (double)loc;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (!((mask >> g) & 1u) || sd[g].row < 0) continue;
+        double tot;
+        if (reduce_last(e, sd[g].row, local[g], tot)) finalize(e, sd[g], tot);
+    }
+}
+
+template <class T, int BD, int KIND, class TO>
+static void launch_one(const Engine& e, const PassDesc* descs, const OpDev& A, const T2<T>* vals,
+                       int npass, cudaStream_t st) {
+    auto k = k_bsr<T, BD, KIND, TO>;
+    dim3 grid(resident_grid((const void*)k, A.nbr), npass);
+    k<<<grid, kThreads, 0, st>>>(e, descs, A, vals);
+}
+
 template <class T, int BD>
 static cudaError_t launch_bd(int kind, int out_f32, const Engine& e, const PassDesc* descs,
-                             const OpDev& A, const T2<T>* vals, dim3 grid, cudaStream_t st) {
+                             const OpDev& A, const T2<T>* vals, int npass, cudaStream_t st) {
     switch (kind) {
-        case PASS_A: k_bsr<T, BD, PASS_A, T><<<grid, kThreads, 0, st>>>(e, descs, A, vals); break;
+        case PASS_A: launch_one<T, BD, PASS_A, T>(e, descs, A, vals, npass, st); break;
         case PASS_C:
-            if (out_f32) k_bsr<T, BD, PASS_C, float><<<grid, kThreads, 0, st>>>(e, descs, A, vals);
-            else k_bsr<T, BD, PASS_C, double><<<grid, kThreads, 0, st>>>(e, descs, A, vals);
+            if (out_f32) launch_one<T, BD, PASS_C, float>(e, descs, A, vals, npass, st);
+            else launch_one<T, BD, PASS_C, double>(e, descs, A, vals, npass, st);
             break;
-        case PASS_D: k_bsr<T, BD, PASS_D, T><<<grid, kThreads, 0, st>>>(e, descs, A, vals); break;
+        case PASS_D: launch_one<T, BD, PASS_D, T>(e, descs, A, vals, npass, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
+template <int BD>
+static void launch_multi(const Engine& e, const PassDesc* descs, int npass, const OpDev& A,
+                         cudaStream_t st) {
+    constexpr int G = 8;
+    auto k = k_bsr_multi<float, BD, G>;
+    dim3 grid(resident_grid((const void*)k, A.nbr), (npass + G - 1) / G);
+    k<<<grid, kThreads, 0, st>>>(e, descs, npass, A, A.vals32);
+}
+
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
-                            const PassDesc* d_descs, int npass, int nblk, cudaStream_t st) {
-    dim3 grid(nblk, npass);
+                            const PassDesc* d_descs, int npass, cudaStream_t st) {
+    if (kind == PASS_A && npass > 1 && prec == PREC_F32) {
+        switch (op.bd) {
+            case 1: launch_multi<1>(e, d_descs, npass, op, st); break;
+            case 2: launch_multi<2>(e, d_descs, npass, op, st); break;
+            default: launch_multi<3>(e, d_descs, npass, op, st); break;
+        }
+        return cudaGetLastError();
+    }
     if (prec == PREC_F64) {
         switch (op.bd) {
-            case 1: return launch_bd<double, 1>(kind, out_f32, e, d_descs, op, op.vals64, grid, st);
-            case 2: return launch_bd<double, 2>(kind, out_f32, e, d_descs, op, op.vals64, grid, st);
-            default: return launch_bd<double, 3>(kind, out_f32, e, d_descs, op, op.vals64, grid, st);
+            case 1: return launch_bd<double, 1>(kind, out_f32, e, d_descs, op, op.vals64, npass, st);
+            case 2: return launch_bd<double, 2>(kind, out_f32, e, d_descs, op, op.vals64, npass, st);
+            default: return launch_bd<double, 3>(kind, out_f32, e, d_descs, op, op.vals64, npass, st);
         }
     }
     if (kind == PASS_C) return cudaErrorInvalidValue;
     switch (op.bd) {
-        case 1: return launch_bd<float, 1>(kind, out_f32, e, d_descs, op, op.vals32, grid, st);
-        case 2: return launch_bd<float, 2>(kind, out_f32, e, d_descs, op, op.vals32, grid, st);
-        default: return launch_bd<float, 3>(kind, out_f32, e, d_descs, op, op.vals32, grid, st);
+        case 1: return launch_bd<float, 1>(kind, out_f32, e, d_descs, op, op.vals32, npass, st);
+        case 2: return launch_bd<float, 2>(kind, out_f32, e, d_descs, op, op.vals32, npass, st);
+        default: return launch_bd<float, 3>(kind, out_f32, e, d_descs, op, op.vals32, npass, st);
     }
 }
 

@@ -31,7 +31,7 @@ struct Buf {
 };
 
 // desc sections, each `rows` entries long
-enum { D_INIT = 0, D_K1, D_K2, D_RUA, D_RUC, D_TRA, D_TRC, D_RIA, D_RIC, D_AP1, D_AP2, D_NSECT };
+enum { D_INIT = 0, D_K1, D_K2, D_RUA, D_RUC, D_RIA, D_RIC, D_AP1, D_AP2, D_NSECT };
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -196,22 +196,18 @@ static PassDesc mkdesc(const void* src, const void* aux, const double2* b, void*
 static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int out_f32, int sec,
                            int npass) {
     Engine e = engine_of(c);
-    const int64_t work = A.kind == OP_STAGGERED ? A.g.V : A.nbr;
-    const int nblk = grid_blocks(work, c->num_sms);
     c->launches++;
     if (A.kind == OP_STAGGERED)
-        return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, nblk, c->work);
-    return launch_bsr_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, nblk, c->work);
+        return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work);
+    return launch_bsr_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work);
 }
 
-static int vec_blocks(msc_ctx* c, int64_t npad) { return grid_blocks(npad / 2, c->num_sms); }
 
 // One chunk of `chunk` iterations for `nsys` systems (+ reliable update).
 static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys, int chunk,
                                  bool reliable, bool profile, int64_t npad, int& kernels) {
     Engine e = engine_of(c);
     VecSet v = vecs_of(c, prec, npad);
-    const int vb = vec_blocks(c, npad);
     kernels = 0;
     for (int it = 0; it < chunk; ++it) {
         const bool prof = profile && it == 0;
@@ -220,16 +216,16 @@ static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys,
         if (err != cudaSuccess) return err;
         if (prof) cudaEventRecordWithFlags(c->prof[1], c->work, cudaEventRecordExternal);
         if (A.kind == OP_STAGGERED) err = op_pass(c, A, prec, PASS_B, 0, D_K2, nsys);
-        else err = launch_axpy_norm(prec, e, v, dsec(c, D_K2), nsys, vb, c->work);
+        else err = launch_axpy_norm(prec, e, v, dsec(c, D_K2), nsys, c->work);
         if (err != cudaSuccess) return err;
         if (prof) cudaEventRecordWithFlags(c->prof[2], c->work, cudaEventRecordExternal);
-        err = launch_update(prec, e, v, nsys, vb, c->work);
+        err = launch_update(prec, e, v, nsys, c->work);
         if (err != cudaSuccess) return err;
         if (prof) cudaEventRecordWithFlags(c->prof[3], c->work, cudaEventRecordExternal);
         kernels += 3;
     }
     if (reliable) {
-        cudaError_t err = launch_fold(e, v, nsys, vb, c->work);
+        cudaError_t err = launch_fold(e, v, nsys, c->work);
         if (err != cudaSuccess) return err;
         kernels++;
         if (A.kind == OP_STAGGERED) {
@@ -318,43 +314,13 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
     return MSC_OK;
 }
 
-// FP64 |b_rhs - (A + sigma_s) x_s|^2 for every slot, into c->h_red.
-static int true_residuals(msc_ctx* c, const msc_op* op, int64_t npad, int nslots, int S,
-                          const double* sigma) {
-    const OpDev& A = op->dev;
-    const double dstag = A.kind == OP_STAGGERED ? A.mass * A.mass : 0.0;
-    double2* x64 = (double2*)c->x64.p;
-    double2* t64 = (double2*)c->t64.p;
-    const double2* b64 = (const double2*)c->b64.p;
-    for (int g = 0; g < nslots; ++g) {
-        const int rhs = g / S, s = g % S;
-        double2* xg = x64 + (size_t)g * npad;
-        const double2* bg = b64 + (size_t)rhs * npad;
-        if (A.kind == OP_STAGGERED) {
-            hsec(c, D_TRA)[g] = mkdesc(xg, nullptr, nullptr, t64 + (size_t)g * npad, 0.0, -1, -1, FIN_NONE);
-            hsec(c, D_TRC)[g] = mkdesc(t64 + (size_t)g * npad, xg, bg, nullptr, dstag + sigma[s], -1, g,
-                                       FIN_STORE);
-        } else {
-            hsec(c, D_TRC)[g] = mkdesc(xg, xg, bg, nullptr, sigma[s], -1, g, FIN_STORE);
-        }
-    }
-    if (A.kind == OP_STAGGERED) {
-        CK(upload_sec(c, D_TRA, nslots));
-        CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_TRA, nslots));
-    }
-    CK(upload_sec(c, D_TRC, nslots));
-    CK(op_pass(c, A, PREC_F64, PASS_C, 0, D_TRC, nslots));
-    CK(cudaMemcpyAsync(c->h_red, c->out_red.p, sizeof(double) * nslots, cudaMemcpyDeviceToHost, c->work));
-    CK(cudaStreamSynchronize(c->work));
-    return MSC_OK;
-}
-
 static void init_sys(SysScalars& s, int S, int base, int slot0, int rhs, double d, double tol,
                      int max_iter, int freeze) {
     memset(&s, 0, sizeof s);
     s.alpha_prev = 1.0;
     s.beta_prev = 0.0;
     s.tol2 = tol * tol;
+    s.tol2_acc = tol * tol;
     s.d = d;
     s.status = ST_RUNNING;
     s.max_iter = max_iter;
@@ -716,8 +682,7 @@ static int apply_impl(msc_ctx* c, const msc_op* op, double sigma, const double* 
         float2* in32 = (float2*)c->r.p;
         float2* mid32 = (float2*)c->t.p;
         float2* out32 = (float2*)c->p.p;
-        const int nb = grid_blocks(n, c->num_sms);
-        CK(launch_convert(in64, 0, in32, 1, n, nb, c->work));
+        CK(launch_convert(in64, 0, in32, 1, n, c->work));
         if (A.kind == OP_STAGGERED) {
             hsec(c, D_AP1)[0] = mkdesc(in32, nullptr, nullptr, mid32, 0.0, -1, -1, FIN_NONE);
             hsec(c, D_AP2)[0] = mkdesc(mid32, in32, nullptr, out32, dstag + sigma, -1, -1, FIN_NONE);
@@ -730,7 +695,7 @@ static int apply_impl(msc_ctx* c, const msc_op* op, double sigma, const double* 
             CK(upload_sec(c, D_AP2, 1));
             CK(op_pass(c, A, PREC_F32, PASS_D, 0, D_AP2, 1));
         }
-        CK(launch_convert(out32, 1, out64, 0, n, nb, c->work));
+        CK(launch_convert(out32, 1, out64, 0, n, c->work));
     }
     CK(cudaMemcpyAsync(out, out64, n * 16, cudaMemcpyDefault, c->work));
     CK(cudaStreamSynchronize(c->work));
@@ -816,8 +781,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     for (int s : {D_INIT, D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, s, nrhs));
     Engine e = engine_of(c);
     VecSet v = vecs_of(c, prec, npad);
-    const int vb = vec_blocks(c, npad);
-    CK(launch_init(prec, e, v, dsec(c, D_INIT), nrhs, vb, c->work));
+    CK(launch_init(prec, e, v, dsec(c, D_INIT), nrhs, c->work));
     c->launches++;
     const int chunk = mixed ? prm.reliable_every : 25;
     ProfAcc pa;
@@ -835,7 +799,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         else if (s.status == ST_ERR_NONFINITE && status != MSC_ERR_NOT_HPD) status = MSC_ERR_NONFINITE;
     }
     if (mixed) {
-        CK(launch_fold(e, v, nrhs, vb, c->work));
+        CK(launch_fold(e, v, nrhs, c->work));
         c->launches++;
     }
     CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslots, cudaMemcpyDeviceToHost, c->work));
@@ -843,25 +807,24 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     std::vector<int> shift_iters(nslots), ref_iters(nslots, 0);
     for (int g = 0; g < nslots; ++g) shift_iters[g] = c->h_slot[g].conv_iter;
     // ---- true residuals and refinement -----------------------------------
-    std::vector<double> rho(nslots, 0.0);
+    // Round r computes, for every shift still to check, the FP64 true residual
+    // b - (A + sigma_s) x_s; that residual is also the start of the shift's
+    // refinement solve (single shift, warm-started from x_s), which runs
+    // unless the shift already meets tol. After `refine` rounds the last
+    // round only checks.
+    std::vector<double> rho(nslots, std::nan(""));
     int rounds = 0, ref_total = 0;
     if (status == MSC_OK) {
-        st = true_residuals(c, op, npad, nslots, S, sigma);
-        if (st) return st;
-        for (int g = 0; g < nslots; ++g) {
-            const double bn2 = bnorm2[g / S];
-            rho[g] = bn2 > 0 ? std::sqrt(c->h_red[g] / bn2) : 0.0;
-        }
-        for (int round = 0; round < prm.refine; ++round) {
-            std::vector<int> todo;
-            for (int g = 0; g < nslots; ++g)
-                if (!(rho[g] <= prm.tol)) todo.push_back(g);
-            if (todo.empty()) break;
+        std::vector<int> todo(nslots);
+        for (int g = 0; g < nslots; ++g) todo[g] = g;
+        for (int round = 0; !todo.empty(); ++round) {
+            const bool check_only = round >= prm.refine;
             const int m = (int)todo.size();
             for (int k = 0; k < m; ++k) {
                 const int g = todo[k], rhs = g / S, s = g % S;
                 const double dk = dstag + sigma[s];
                 init_sys(c->h_sys[k], 1, 0, g, rhs, dk, 0.5 * prm.tol, prm.max_iter, 1);
+                c->h_sys[k].tol2_acc = prm.tol * prm.tol;
                 c->h_sys[k].bnorm2 = bnorm2[rhs];
                 init_slot(c->h_slot[g], 0.0);
                 const double2* bj = b64 + (size_t)rhs * npad;
@@ -889,7 +852,19 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
             for (int s : {D_RIA, D_RIC, D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, s, m));
             if (A.kind == OP_STAGGERED) CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_RIA, m));
             CK(op_pass(c, A, PREC_F64, PASS_C, mixed ? 1 : 0, D_RIC, m));
-            CK(launch_init_from_r(prec, e, v, m, vb, c->work));
+            CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * m, cudaMemcpyDeviceToHost, c->work));
+            CK(cudaStreamSynchronize(c->work));
+            std::vector<int> next;
+            for (int k = 0; k < m; ++k) {
+                const SysScalars& s = c->h_sys[k];
+                const int g = todo[k];
+                const double bn2 = bnorm2[g / S];
+                rho[g] = bn2 > 0 ? std::sqrt(s.R / bn2) : 0.0;
+                if (s.status == ST_ERR_NONFINITE) status = MSC_ERR_NONFINITE;
+                else if (s.status == ST_RUNNING) next.push_back(g);
+            }
+            if (check_only || next.empty() || status != MSC_OK) break;
+            CK(launch_init_from_r(prec, e, v, m, c->work));
             c->launches++;
             st = run_stage(c, op, prec, m, chunk, mixed, false, npad, prm.max_iter, nullptr, &rel);
             if (st) return st;
@@ -904,16 +879,11 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
             ref_total += most;
             rounds++;
             if (mixed) {
-                CK(launch_fold(e, v, m, vb, c->work));
+                CK(launch_fold(e, v, m, c->work));
                 c->launches++;
             }
             if (status != MSC_OK) break;
-            st = true_residuals(c, op, npad, nslots, S, sigma);
-            if (st) return st;
-            for (int g = 0; g < nslots; ++g) {
-                const double bn2 = bnorm2[g / S];
-                rho[g] = bn2 > 0 ? std::sqrt(c->h_red[g] / bn2) : 0.0;
-            }
+            todo = next;
         }
         if (status == MSC_OK) {
             for (int g = 0; g < nslots; ++g)
@@ -1012,9 +982,8 @@ extern "C" int msc_op_apply_noalloc(const msc_op* op, double sigma, const double
         k_noalloc_store_descs<<<1, 32, 0, st>>>(descs, d1, d2);
         cudaError_t e = cudaGetLastError();
         Engine none{};
-        const int nblk = grid_blocks(A.g.V, op->ctx->num_sms);
-        if (e == cudaSuccess) e = launch_stag_pass(A, PREC_F64, PASS_A, 0, none, descs, 1, nblk, st);
-        if (e == cudaSuccess) e = launch_stag_pass(A, PREC_F64, PASS_D, 0, none, descs + 1, 1, nblk, st);
+        if (e == cudaSuccess) e = launch_stag_pass(A, PREC_F64, PASS_A, 0, none, descs, 1, st);
+        if (e == cudaSuccess) e = launch_stag_pass(A, PREC_F64, PASS_D, 0, none, descs + 1, 1, st);
         if (e != cudaSuccess) status = cuda_status(e);
     }
     if (prev != dev) cudaSetDevice(prev);

@@ -3,6 +3,11 @@
 // Every update in the iteration is a real scalar times a complex vector, so
 // the kernels treat a vector as a flat array of reals and move it in 16-byte
 // units (float4 = two complex FP32 values, double2 = one complex FP64 value).
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "engine.h"
 
 namespace msc {
@@ -108,10 +113,15 @@ __global__ void __launch_bounds__(kThreads) k_init_from_r(Engine e, VecSet v) {
 // The fused multi-shift update (Algorithm 1, lines 28-29, plus p): for every
 // shift still iterating, x_s += alpha_s p_s and p_s = zeta_s' r + beta_s p_s;
 // the base shift's direction is p itself, so only its x moves; then
-// p = r + beta p. One read of r and p serves every shift.
+// p = r + beta p. One read of r and p serves every shift. Each thread keeps
+// U units of r and p in registers and issues the loads of one shift for all
+// U units before using them, so enough bytes are in flight per SM.
+constexpr int kUnits = 4;
+
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v) {
     using V = typename U16<T>::t;
+    constexpr int U = kUnits;
     const int j = blockIdx.y;
     SysScalars* s = &e.sys[j];
     const int st = load_status(s);
@@ -133,23 +143,54 @@ __global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v) {
     V* __restrict__ p = (V*)v.p + (size_t)j * upv;
     V* __restrict__ ps = (V*)v.ps + (size_t)slot0 * upv;
     V* __restrict__ xs = (V*)v.xit + (size_t)slot0 * upv;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const V ri = r[i];
-        const V pi = p[i];
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < upv; i0 += step * U) {
+        V rv[U], pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * step;
+            if (i < upv) {
+                rv[u] = r[i];
+                pv[u] = p[i];
+            }
+        }
         for (int k = 0; k < S; ++k) {
             const int f = sf[k];
             if (f == 0) continue;
-            const size_t g = (size_t)k * upv + i;
+            V* __restrict__ xk = xs + (size_t)k * upv;
+            V xv[U], pk[U];
             if (k == base) {
-                xs[g] = axpy(sa[k], pi, xs[g]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (i0 + u * step < upv) xv[u] = xk[i0 + u * step];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (i0 + u * step < upv) xk[i0 + u * step] = axpy(sa[k], pv[u], xv[u]);
                 continue;
             }
-            const V pk = ps[g];
-            xs[g] = axpy(sa[k], pk, xs[g]);
-            if (f == 2) ps[g] = axpby(sz[k], ri, sb[k], pk);
+            V* __restrict__ pks = ps + (size_t)k * upv;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = i0 + u * step;
+                if (i < upv) {
+                    pk[u] = pks[i];
+                    xv[u] = xk[i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = i0 + u * step;
+                if (i < upv) {
+                    xk[i] = axpy(sa[k], pk[u], xv[u]);
+                    if (f == 2) pks[i] = axpby(sz[k], rv[u], sb[k], pk[u]);
+                }
+            }
         }
-        p[i] = axpy(beta, pi, ri);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * step;
+            if (i < upv) p[i] = axpy(beta, pv[u], rv[u]);
+        }
     }
     if (arrive_last(e, j)) {
         if (threadIdx.x == 0 && s->status == ST_FINISHING) s->status = ST_DONE;
@@ -160,6 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v) {
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, const PassDesc* descs) {
     using V = typename U16<T>::t;
+    constexpr int U = kUnits;
     const PassDesc d = descs[blockIdx.y];
     if (gated_off(e, d)) return;
     const int j = d.sys;
@@ -168,11 +210,26 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, cons
     V* __restrict__ r = (V*)v.r + (size_t)j * upv;
     const V* __restrict__ ap = (const V*)v.t + (size_t)j * upv;
     double local = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const V rv = axpy(na, ap[i], r[i]);
-        r[i] = rv;
-        local += (double)sq(rv);
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < upv; i0 += step * U) {
+        V rv[U], av[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * step;
+            if (i < upv) {
+                rv[u] = r[i];
+                av[u] = ap[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * step;
+            if (i < upv) {
+                const V nv = axpy(na, av[u], rv[u]);
+                r[i] = nv;
+                local += (double)sq(nv);
+            }
+        }
     }
     double tot;
     if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
@@ -223,47 +280,76 @@ int grid_blocks(int64_t work, int num_sms) {
     return (int)b;
 }
 
+int resident_grid(const void* fn, int64_t work) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int cap;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find({fn, dev});
+        if (it == cache.end()) {
+            int per_sm = 0, sms = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cap = std::max(1, per_sm) * std::max(1, sms);
+            if (cap > kMaxBlocks) cap = kMaxBlocks;
+            cache[{fn, dev}] = cap;
+        } else {
+            cap = it->second;
+        }
+    }
+    int64_t b = (work + kThreads - 1) / kThreads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <class K>
+static dim3 vgrid(K kernel, int64_t upv, int units_per_thread, int nsys) {
+    return dim3(resident_grid((const void*)kernel, (upv + units_per_thread - 1) / units_per_thread), nsys);
+}
+
+static int64_t upv_of(int prec, const VecSet& v) { return prec == PREC_F32 ? v.npad / 2 : v.npad; }
+
 cudaError_t launch_init(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
-                        int nsys, int nblk, cudaStream_t st) {
-    dim3 grid(nblk, nsys);
-    if (prec == PREC_F32) k_init<float><<<grid, kThreads, 0, st>>>(e, v, d_descs);
-    else k_init<double><<<grid, kThreads, 0, st>>>(e, v, d_descs);
+                        int nsys, cudaStream_t st) {
+    if (prec == PREC_F32) k_init<float><<<vgrid(k_init<float>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs);
+    else k_init<double><<<vgrid(k_init<double>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int nsys, int nblk,
-                               cudaStream_t st) {
-    dim3 grid(nblk, nsys);
-    if (prec == PREC_F32) k_init_from_r<float><<<grid, kThreads, 0, st>>>(e, v);
-    else k_init_from_r<double><<<grid, kThreads, 0, st>>>(e, v);
+cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st) {
+    if (prec == PREC_F32) k_init_from_r<float><<<vgrid(k_init_from_r<float>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v);
+    else k_init_from_r<double><<<vgrid(k_init_from_r<double>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, int nblk,
-                          cudaStream_t st) {
-    dim3 grid(nblk, nsys);
-    if (prec == PREC_F32) k_update<float><<<grid, kThreads, 0, st>>>(e, v);
-    else k_update<double><<<grid, kThreads, 0, st>>>(e, v);
+cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st) {
+    if (prec == PREC_F32) k_update<float><<<vgrid(k_update<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v);
+    else k_update<double><<<vgrid(k_update<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
-                             int nsys, int nblk, cudaStream_t st) {
-    dim3 grid(nblk, nsys);
-    if (prec == PREC_F32) k_axpy_norm<float><<<grid, kThreads, 0, st>>>(e, v, d_descs);
-    else k_axpy_norm<double><<<grid, kThreads, 0, st>>>(e, v, d_descs);
+                             int nsys, cudaStream_t st) {
+    if (prec == PREC_F32) k_axpy_norm<float><<<vgrid(k_axpy_norm<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs);
+    else k_axpy_norm<double><<<vgrid(k_axpy_norm<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int nblk, cudaStream_t st) {
-    dim3 grid(nblk, nsys);
-    k_fold<<<grid, kThreads, 0, st>>>(e, v);
+cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, cudaStream_t st) {
+    k_fold<<<vgrid(k_fold, v.npad / 2, 1, nsys), kThreads, 0, st>>>(e, v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n,
-                           int nblk, cudaStream_t st) {
-    k_convert<<<nblk, kThreads, 0, st>>>(src, src_f32, dst, dst_f32, n);
+                           cudaStream_t st) {
+    k_convert<<<resident_grid((const void*)k_convert, n), kThreads, 0, st>>>(src, src_f32, dst, dst_f32, n);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,7 @@ struct SysScalars {
     double bnorm2;    // |b|^2
     double tol2;      // tol^2
     double d;         // diagonal shift of the operator pass (m^2+sigma0 or sigma0)
+    double tol2_acc;  // start-of-solve acceptance: done at once if R <= tol2_acc |b|^2
     int status, it, max_iter, capped;
     int S, base, slot0, rhs;
     int freeze, pad0, pad1, pad2;
@@ -110,6 +111,21 @@ template <class T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return {a.x
 template <class T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return {a.x - b.x, a.y - b.y}; }
 template <class T2, class T> __device__ __forceinline__ T2 cscale(T s, T2 a) { return {s * a.x, s * a.y}; }
 template <class T2> __device__ __forceinline__ T2 cconj(T2 a) { return {a.x, -a.y}; }
+
+// acc += a b, as four fused multiply-adds
+template <class T2> __device__ __forceinline__ void cfma(T2& acc, T2 a, T2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc -= conj(a) b, as four fused multiply-adds
+template <class T2> __device__ __forceinline__ void cfms_conj(T2& acc, T2 a, T2 b) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
 
 __device__ __forceinline__ int load_status(const SysScalars* s) {
     return __ldcg(&s->status);
@@ -247,7 +263,7 @@ __device__ __forceinline__ void fin_R(const Engine& e, int j, double Rn) {
 // already meets the tolerance is done with nothing to iterate.
 __device__ __forceinline__ void fin_setR(const Engine& e, int j, double Rv, bool init) {
     SysScalars* s = &e.sys[j];
-    const double thr = s->tol2 * s->bnorm2;
+    const double thr = s->tol2_acc * s->bnorm2;
     const int S = s->S, slot0 = s->slot0;
     __syncthreads();
     if (!isfinite(Rv)) {

@@ -45,9 +45,9 @@ struct OpDev {
 
 // kernel launchers (return the launch error)
 cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
-                             const PassDesc* d_descs, int npass, int nblk, cudaStream_t st);
+                             const PassDesc* d_descs, int npass, cudaStream_t st);
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
-                            const PassDesc* d_descs, int npass, int nblk, cudaStream_t st);
+                            const PassDesc* d_descs, int npass, cudaStream_t st);
 
 // vector kernels; vectors are addressed as [index][npad] complex in the
 // iteration precision (prec) unless noted
@@ -62,16 +62,14 @@ struct VecSet {
     int64_t npad;
 };
 cudaError_t launch_init(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
-                        int nsys, int nblk, cudaStream_t st);
-cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int nsys, int nblk,
-                               cudaStream_t st);
-cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, int nblk,
-                          cudaStream_t st);
+                        int nsys, cudaStream_t st);
+cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st);
+cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st);
 cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
-                             int nsys, int nblk, cudaStream_t st);
-cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int nblk, cudaStream_t st);
+                             int nsys, cudaStream_t st);
+cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, cudaStream_t st);
 cudaError_t launch_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n,
-                           int nblk, cudaStream_t st);
+                           cudaStream_t st);
 
 // set-up kernels
 cudaError_t stag_pack_links(OpDev& op, const double2* links_aos, double* d_maxdev,
@@ -85,5 +83,9 @@ cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
                      const double2* d_vals, int* d_bad, cudaStream_t st);
 
 int grid_blocks(int64_t work, int num_sms);
+
+// Blocks of kThreads for `work` items: one item per thread, capped at the
+// blocks that fit on the device at once for kernel `fn` (no partial waves).
+int resident_grid(const void* fn, int64_t work);
 
 }  // namespace msc

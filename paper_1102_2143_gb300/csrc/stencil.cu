@@ -113,11 +113,11 @@ __device__ __forceinline__ void dslash_site(const void* links, const T2<T>* __re
             T2<T> f = {T(0), T(0)};
 #pragma unroll
             for (int b = 0; b < NC; ++b) {
-                f = cadd(f, cmul(u[a][b], v[b]));    // U_mu(x) src(x+mu)
-                f = csub(f, cmulc(w[b][a], z[b]));   // U_mu(x-mu)^dag src(x-mu)
+                cfma(f, u[a][b], v[b]);        // + U_mu(x) src(x+mu)
+                cfms_conj(f, w[b][a], z[b]);   // - U_mu(x-mu)^dag src(x-mu)
             }
-            y[a].x += eta * f.x;
-            y[a].y += eta * f.y;
+            y[a].x = fma(eta, f.x, y[a].x);
+            y[a].y = fma(eta, f.y, y[a].y);
         }
     }
 }
@@ -196,35 +196,42 @@ __global__ void __launch_bounds__(kThreads) k_stag(Engine e, const PassDesc* des
     }
 }
 
+template <class T, int NC, int RECON, int KIND, class TO>
+static void launch_one(const Engine& e, const PassDesc* descs, StagGeom g, const void* links, int npass,
+                       cudaStream_t st) {
+    auto k = k_stag<T, NC, RECON, KIND, TO>;
+    dim3 grid(resident_grid((const void*)k, g.V), npass);
+    k<<<grid, kThreads, 0, st>>>(e, descs, g, links);
+}
+
 template <class T, int NC, int RECON>
 static cudaError_t launch_kind(int kind, int out_f32, const Engine& e, const PassDesc* descs,
-                               StagGeom g, const void* links, dim3 grid, cudaStream_t st) {
+                               StagGeom g, const void* links, int npass, cudaStream_t st) {
     switch (kind) {
-        case PASS_A: k_stag<T, NC, RECON, PASS_A, T><<<grid, kThreads, 0, st>>>(e, descs, g, links); break;
-        case PASS_B: k_stag<T, NC, RECON, PASS_B, T><<<grid, kThreads, 0, st>>>(e, descs, g, links); break;
+        case PASS_A: launch_one<T, NC, RECON, PASS_A, T>(e, descs, g, links, npass, st); break;
+        case PASS_B: launch_one<T, NC, RECON, PASS_B, T>(e, descs, g, links, npass, st); break;
         case PASS_C:
-            if (out_f32) k_stag<T, NC, RECON, PASS_C, float><<<grid, kThreads, 0, st>>>(e, descs, g, links);
-            else k_stag<T, NC, RECON, PASS_C, double><<<grid, kThreads, 0, st>>>(e, descs, g, links);
+            if (out_f32) launch_one<T, NC, RECON, PASS_C, float>(e, descs, g, links, npass, st);
+            else launch_one<T, NC, RECON, PASS_C, double>(e, descs, g, links, npass, st);
             break;
-        default: k_stag<T, NC, RECON, PASS_D, T><<<grid, kThreads, 0, st>>>(e, descs, g, links); break;
+        default: launch_one<T, NC, RECON, PASS_D, T>(e, descs, g, links, npass, st); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
-                             const PassDesc* d_descs, int npass, int nblk, cudaStream_t st) {
-    dim3 grid(nblk, npass);
+                             const PassDesc* d_descs, int npass, cudaStream_t st) {
     if (prec == PREC_F64) {
-        if (op.nc == 3) return launch_kind<double, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links64, grid, st);
-        return launch_kind<double, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links64, grid, st);
+        if (op.nc == 3) return launch_kind<double, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links64, npass, st);
+        return launch_kind<double, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links64, npass, st);
     }
     if (kind == PASS_C) return cudaErrorInvalidValue;  // residual passes run in FP64
     if (op.nc == 3) {
-        if (op.recon) return launch_kind<float, 3, 1>(kind, out_f32, e, d_descs, op.g, op.links32, grid, st);
-        return launch_kind<float, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links32, grid, st);
+        if (op.recon) return launch_kind<float, 3, 1>(kind, out_f32, e, d_descs, op.g, op.links32, npass, st);
+        return launch_kind<float, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links32, npass, st);
     }
-    if (op.recon) return launch_kind<float, 2, 1>(kind, out_f32, e, d_descs, op.g, op.links32, grid, st);
-    return launch_kind<float, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links32, grid, st);
+    if (op.recon) return launch_kind<float, 2, 1>(kind, out_f32, e, d_descs, op.g, op.links32, npass, st);
+    return launch_kind<float, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links32, npass, st);
 }
 
 // ---------------------------------------------------------------------------
