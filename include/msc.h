@@ -199,6 +199,26 @@ int msc_solve(msc_ctx* ctx, const msc_op* op, const double* b, int nrhs,
               const double* sigma, int S, const msc_params* params, double* x,
               msc_info* info);
 
+/* Rational pseudofermion action and its adjoint (the quadratic form that the
+ * shifted family diagonalises, Sec. 1-2; sigma_s and c_s come from a rational
+ * approximation):  S = sum_s c_s Re(phi^dagger x_s),  x_s = (A + sigma_s)^{-1} phi.
+ * msc_quad_form: *value = S for solved x_s. phi: [n] complex; coef: [S]
+ * host array of c_s; x: [S][n] complex (e.g. msc_solve's output for one
+ * right-hand side). FP64 on the device. */
+int msc_quad_form(msc_ctx* ctx, const msc_op* op, const double* phi, int S, const double* coef,
+                  const double* x, double* value);
+
+/* Gradients of S, in the convention grad = dS/dRe + i dS/dIm of each complex
+ * entry (the one torch.autograd uses for a real loss of complex inputs):
+ *   dphi = 2 sum_s c_s x_s                                     ([n] complex)
+ *   dU_mu(x) = sum_s c_s eta_mu(x) [x_s(x) y_s(x+mu)^dagger - y_s(x) x_s(x+mu)^dagger],
+ *   y_s = D x_s   ([4][V][nc][nc] complex, staggered operators only),
+ * treating the link entries as free complex variables (no projection onto
+ * SU(N)). Derived from dS = -sum_s c_s x_s^dagger dA x_s with dA = -(dD D + D dD).
+ * Either output may be NULL; outputs may be host or device. FP64. */
+int msc_quad_form_grad(msc_ctx* ctx, const msc_op* op, int S, const double* coef, const double* x,
+                       double* dphi, double* dU);
+
 const char* msc_strerror(int code);
 
 #ifdef __cplusplus

@@ -87,6 +87,8 @@ SIGNATURES = {
     "msc_solve": (_I, [_VP, _VP, _VP, _I, _VP, _I, ctypes.POINTER(msc_params), _VP,
                        ctypes.POINTER(msc_info)]),
     "msc_strerror": (ctypes.c_char_p, [_I]),
+    "msc_quad_form": (_I, [_VP, _VP, _VP, _I, _VP, _VP, ctypes.POINTER(_D)]),
+    "msc_quad_form_grad": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
 }
 
 
@@ -220,6 +222,36 @@ def msc_op_apply_noalloc(op: int, sigma: float, x, out, stream=None) -> None:
 
 def msc_op_destroy(op: int) -> None:
     _check(load().msc_op_destroy(op), "msc_op_destroy")
+
+
+def msc_quad_form(ctx: int, op: int, phi, S: int, coef, x) -> float:
+    """S = sum_s c_s Re(phi^dag x_s) on the device (x: [S][n] solved x_s)."""
+    cf = np.ascontiguousarray(coef, dtype=np.float64)
+    v = ctypes.c_double()
+    _check(load().msc_quad_form(ctx, op, _ptr(phi), int(S), _ptr(cf), _ptr(x), ctypes.byref(v)),
+           "msc_quad_form")
+    return v.value
+
+
+def msc_quad_form_grad(ctx: int, op: int, S: int, coef, x, dphi=None, dU=None) -> None:
+    """dphi = 2 sum_s c_s x_s and the link force dU (see include/msc.h)."""
+    cf = np.ascontiguousarray(coef, dtype=np.float64)
+    _check(load().msc_quad_form_grad(ctx, op, int(S), _ptr(cf), _ptr(x), _ptr(dphi), _ptr(dU)),
+           "msc_quad_form_grad")
+
+
+_contexts = {}
+
+
+def default_context(device: int = 0) -> int:
+    """A context per device for the convenience and autograd layers."""
+    with _lock:
+        h = _contexts.get(device)
+    if h is None:
+        h = msc_create(device, None)
+        with _lock:
+            _contexts[device] = h
+    return h
 
 
 def msc_params_default() -> msc_params:

@@ -53,6 +53,7 @@ struct msc_ctx {
     // device workspace (grow only; `gen` changes whenever a buffer moves)
     Buf sys, slot, partial, counter, out_red, descs;
     Buf b64, x64, t64, r, p, t, ps, xit;
+    Buf coef, force;  // adjoint: weights c_s and a link-shaped output
     int64_t rows_cap = 0;  // rows the desc sections were laid out for
     int gen = 0;
     // pinned host mirrors
@@ -404,7 +405,8 @@ int msc_destroy(msc_ctx* c) {
     for (auto& kv : c->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     Buf* bufs[] = {&c->sys, &c->slot, &c->partial, &c->counter, &c->out_red, &c->descs,
-                   &c->b64, &c->x64, &c->t64, &c->r, &c->p, &c->t, &c->ps, &c->xit};
+                   &c->b64, &c->x64, &c->t64, &c->r, &c->p, &c->t, &c->ps, &c->xit,
+                   &c->coef, &c->force};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_sys) cudaFreeHost(c->h_sys);
@@ -915,6 +917,81 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adjoint of S = sum_s c_s Re(phi^dag x_s) (rational pseudofermion action)
+// ---------------------------------------------------------------------------
+static int stage_solutions(msc_ctx* c, const msc_op* op, int S, const double* coef, const double* x,
+                           int64_t& n, int64_t& npad) {
+    n = op->dev.n;
+    npad = (n + 63) / 64 * 64;
+    int st = ensure_ws(c, npad, std::max(S, 3), S, 1, 16);
+    if (st) return st;
+    bool moved = false;
+    CK(grow(c->coef, sizeof(double) * S, moved));
+    CK(cudaMemcpyAsync(c->coef.p, coef, sizeof(double) * S, cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpy2DAsync(c->x64.p, npad * 16, x, n * 16, n * 16, S, cudaMemcpyDefault, c->work));
+    return MSC_OK;
+}
+
+extern "C" int msc_quad_form(msc_ctx* c, const msc_op* op, const double* phi, int S, const double* coef,
+                             const double* x, double* value) {
+    if (!c || !op || !phi || !coef || !x || !value || S <= 0) return MSC_ERR_ARG;
+    int st = begin(c);
+    if (st) return st;
+    int64_t n, npad;
+    st = stage_solutions(c, op, S, coef, x, n, npad);
+    if (st) return st;
+    double2* phi64 = (double2*)c->b64.p;
+    CK(cudaMemcpyAsync(phi64, phi, n * 16, cudaMemcpyDefault, c->work));
+    CK(launch_quad(engine_of(c), phi64, (const double2*)c->x64.p, (const double*)c->coef.p, S, n, npad, 0,
+                   c->work));
+    c->launches++;
+    CK(cudaMemcpyAsync(value, c->out_red.p, sizeof(double), cudaMemcpyDeviceToHost, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    return MSC_OK;
+}
+
+extern "C" int msc_quad_form_grad(msc_ctx* c, const msc_op* op, int S, const double* coef,
+                                  const double* x, double* dphi, double* dU) {
+    if (!c || !op || !coef || !x || S <= 0 || (!dphi && !dU)) return MSC_ERR_ARG;
+    if (dU && op->dev.kind != OP_STAGGERED) return MSC_ERR_ARG;
+    int st = begin(c);
+    if (st) return st;
+    int64_t n, npad;
+    st = stage_solutions(c, op, S, coef, x, n, npad);
+    if (st) return st;
+    const double2* x64 = (const double2*)c->x64.p;
+    double2* t64 = (double2*)c->t64.p;
+    const double* dc = (const double*)c->coef.p;
+    if (dphi) {
+        CK(launch_dphi(x64, dc, S, n, npad, t64, c->work));
+        c->launches++;
+        CK(cudaMemcpyAsync(dphi, t64, n * 16, cudaMemcpyDefault, c->work));
+    }
+    if (dU) {
+        const OpDev& A = op->dev;
+        // y_s = D x_s for every shift (FP64 D pass), then the outer products
+        for (int s = 0; s < S; ++s)
+            hsec(c, D_AP1)[s] = mkdesc(x64 + (size_t)s * npad, nullptr, nullptr, t64 + (size_t)s * npad, 0.0,
+                                       -1, -1, FIN_NONE);
+        CK(upload_sec(c, D_AP1, S));
+        CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_AP1, S));
+        const size_t gbytes = (size_t)4 * A.g.V * A.nc * A.nc * 16;
+        double2* G = (double2*)dU;
+        const bool dev_out = is_device_ptr(dU);
+        if (!dev_out) {
+            bool moved = false;
+            CK(grow(c->force, gbytes, moved));
+            G = (double2*)c->force.p;
+        }
+        CK(launch_force(A, x64, t64, dc, S, npad, G, c->work));
+        c->launches++;
+        if (!dev_out) CK(cudaMemcpyAsync(dU, G, gbytes, cudaMemcpyDeviceToHost, c->work));
+    }
+    CK(cudaStreamSynchronize(c->work));
+    return MSC_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Operator apply that allocates nothing.

@@ -82,6 +82,14 @@ cudaError_t stag_export_bsr(const OpDev& op, int64_t* row_ptr, int32_t* col, dou
 cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
                      const double2* d_vals, int* d_bad, cudaStream_t st);
 
+// adjoint (force.cu)
+cudaError_t launch_quad(const Engine& e, const double2* phi, const double2* x, const double* c, int S,
+                        int64_t n, int64_t npad, int row, cudaStream_t st);
+cudaError_t launch_dphi(const double2* x, const double* c, int S, int64_t n, int64_t npad,
+                        double2* out, cudaStream_t st);
+cudaError_t launch_force(const OpDev& op, const double2* x, const double2* y, const double* c, int S,
+                         int64_t npad, double2* G, cudaStream_t st);
+
 int grid_blocks(int64_t work, int num_sms);
 
 // Blocks of kThreads for `work` items: one item per thread, capped at the
