@@ -69,15 +69,15 @@ def solve_bytes(info, S, nnzb, bd, n, mixed=True, reliable_every=50, group=8):
       r -= alpha Ap with |r|^2: 3 passes;
       update: r, p read + p write (3), every non-base shift still active
       4 passes (3 in its last iteration), the base shift's x 2 passes.
-    Mixed only: at every chunk end (reliable_every iterations) a fold of
-      each shift's FP32 x into FP64 (x32 read, x64 read+write = 40 B per
-      unknown) and, while running, one FP64 residual SpMV (+ b read, r write).
+    Mixed only: at every reliable update (the count is reported by the
+      library) a fold of each shift's FP32 x into FP64 (x32 read, x64
+      read+write = 40 B per unknown; one shift in the refinement stage) and
+      one FP64 residual SpMV (+ b read, r write).
     Checks: each check round applies the FP64 operator to every shift it
       checks (round 0: all S; later rounds: the shifts just refined).
     Refinement iteration k: the SpMV reads the matrix once per group of
       `group` refined shifts with one still iterating, plus source and output
-      per iterating shift; r update 3 passes and update 5 passes per shift;
-      mixed: reliable update and fold every reliable_every iterations.
+      per iterating shift; r update 3 passes and update 5 passes per shift.
     """
     rb = 4 if mixed else 8
     c = 2 * rb
@@ -97,8 +97,12 @@ def solve_bytes(info, S, nnzb, bd, n, mixed=True, reliable_every=50, group=8):
             upd += 4 if k < cs else (3 if k == cs else 0)
         total += a_it + (3 + upd) * n * c
     if mixed:
-        chunks = -(-it // reliable_every) if it else 0
-        total += (chunks + 1) * S * 40 * n + max(chunks - 1, 0) * a64
+        # reliable updates of the multi-shift stage (fold every shift) and the
+        # final fold of the stage
+        ru_main = int(info.reliable_updates) - int(info.refine_reliable_updates)
+        total += (ru_main + 1) * S * 40 * n + ru_main * a64
+        # refinement-stage updates: fold one shift each
+        total += int(info.refine_reliable_updates) * (a64 + 40 * n)
     ref = np.asarray(info.shift_refine_iters).reshape(-1)
     refined = int(np.count_nonzero(ref))
     total += (S + refined * int(info.refine_rounds)) * a64
@@ -107,8 +111,6 @@ def solve_bytes(info, S, nnzb, bd, n, mixed=True, reliable_every=50, group=8):
         act = [s for s in range(len(ref)) if ref[s] >= k]
         groups = len({s // group for s in act})
         total += groups * mat + len(act) * (2 + 3 + 5) * n * c
-        if mixed and k % reliable_every == 0:
-            total += len(act) * (a64 + 40 * n)
     return total
 
 

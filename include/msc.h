@@ -150,16 +150,22 @@ typedef struct {
     double tol;          /* relative residual target per shift: |b-(A+s)x_s| <= tol |b| */
     int max_iter;        /* cap on multi-shift iterations (and per refinement round) */
     int precision;       /* MSC_FP64 or MSC_MIXED */
-    int reliable_every;  /* MSC_MIXED: FP64 reliable update every this many iterations */
+    int reliable_every;  /* MSC_MIXED: FP64 reliable update at the latest after this
+                            many iterations since the last one */
     int freeze_converged;/* 1: stop updating a shift once it meets tol (default);
                             0: update every shift until all meet tol */
     int refine;          /* max refinement rounds after the multi-shift solve
                             (0 = none); a round re-solves each shift whose FP64
                             true residual is above tol, warm-started from x_s */
+    double reliable_delta;/* MSC_MIXED: FP64 reliable update as soon as the iterated
+                            residual norm falls below reliable_delta times its
+                            largest value since the last update (0 <= delta < 1;
+                            0: only the iteration count triggers it). Keeps the
+                            FP32 drift small next to the residual it corrupts. */
 } msc_params;
 
 /* Fill defaults: tol 1e-10, max_iter 100000, MSC_MIXED, reliable_every 50,
- * freeze 1, refine 4. */
+ * freeze 1, refine 4, reliable_delta 0.01. */
 void msc_params_default(msc_params* p);
 
 typedef struct {
@@ -168,7 +174,8 @@ typedef struct {
     int refine_rounds;      /* refinement rounds run */
     int refine_iters;       /* refinement iterations (sum over rounds of the
                                max over the systems refined in that round) */
-    int reliable_updates;   /* FP64 reliable updates run (all stages) */
+    int reliable_updates;   /* FP64 reliable updates done (all systems, all stages) */
+    int refine_reliable_updates; /* of which in the refinement stage */
     int kernel_launches;    /* kernels launched by this solve */
     double seconds;         /* host wall time of the call */
     /* optional caller arrays of nrhs*S entries (index rhs*S + s), or NULL */
@@ -218,6 +225,40 @@ int msc_quad_form(msc_ctx* ctx, const msc_op* op, const double* phi, int S, cons
  * Either output may be NULL; outputs may be host or device. FP64. */
 int msc_quad_form_grad(msc_ctx* ctx, const msc_op* op, int S, const double* coef, const double* x,
                        double* dphi, double* dU);
+
+/* Batched uneven systems: many independent staggered problems, each with
+ * its own operator (any lattice, SU(2) or SU(3)), shift list and number of
+ * right-hand sides, solved together: every pass of the iteration is one
+ * kernel launch for the whole batch (blocks are divided among the systems in
+ * proportion to their size), chunks of iterations are CUDA graphs, and each
+ * system keeps its own recurrences, convergence and refinement. */
+typedef struct {
+    const msc_op* op;      /* staggered operator created on the same context */
+    const double* b;       /* [nrhs][n] complex, host or device */
+    int nrhs;
+    const double* sigma;   /* [S] host array, each >= 0 */
+    int S;
+    double* x;             /* [nrhs][S][n] complex out, host or device */
+    msc_info* info;        /* optional report for this problem (arrays nrhs*S) */
+} msc_problem;
+
+/* Launch shapes picked by the autotuner for a batch: it times candidate
+ * block sizes of the operator pass and block sizes x units per thread of the
+ * multi-shift update on the batch itself before the solve, and reuses the
+ * winner for later batches of the same shape (same process). */
+typedef struct {
+    int site_threads;      /* threads per block of the operator passes */
+    int vec_threads;       /* threads per block of the vector kernels */
+    int vec_units;         /* 16-byte units per thread of the update */
+    int tuned;             /* 1: measured for this call, 0: from the cache */
+    double best_ms;        /* operator pass + update time of the winner */
+} msc_tuning;
+
+/* Solve every problem of the batch. Returns the worst status over the
+ * problems (MSC_ERR_NOT_CONVERGED if any shift missed tol); each problem's
+ * info holds its own status. `tuning` may be NULL. */
+int msc_solve_batched(msc_ctx* ctx, int nprob, const msc_problem* probs, const msc_params* params,
+                      msc_tuning* tuning);
 
 const char* msc_strerror(int code);
 

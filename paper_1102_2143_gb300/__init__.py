@@ -50,18 +50,30 @@ class MscError(RuntimeError):
 class msc_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("reliable_every", ctypes.c_int), ("freeze_converged", ctypes.c_int),
-                ("refine", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("reliable_delta", ctypes.c_double)]
 
 
 class msc_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refine_rounds", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("refine_reliable_updates", ctypes.c_int),
                 ("kernel_launches", ctypes.c_int), ("seconds", ctypes.c_double),
                 ("shift_iters", ctypes.POINTER(ctypes.c_int)),
                 ("shift_refine_iters", ctypes.POINTER(ctypes.c_int)),
                 ("true_rel_resid", ctypes.POINTER(ctypes.c_double)),
                 ("op_ms", ctypes.c_double), ("rupdate_ms", ctypes.c_double),
                 ("update_ms", ctypes.c_double), ("prof_samples", ctypes.c_int)]
+
+
+class msc_problem(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_void_p), ("b", ctypes.c_void_p), ("nrhs", ctypes.c_int),
+                ("sigma", ctypes.c_void_p), ("S", ctypes.c_int), ("x", ctypes.c_void_p),
+                ("info", ctypes.POINTER(msc_info))]
+
+
+class msc_tuning(ctypes.Structure):
+    _fields_ = [("site_threads", ctypes.c_int), ("vec_threads", ctypes.c_int),
+                ("vec_units", ctypes.c_int), ("tuned", ctypes.c_int), ("best_ms", ctypes.c_double)]
 
 
 # exported symbols of include/msc.h with their ctypes signatures
@@ -89,6 +101,7 @@ SIGNATURES = {
     "msc_strerror": (ctypes.c_char_p, [_I]),
     "msc_quad_form": (_I, [_VP, _VP, _VP, _I, _VP, _VP, ctypes.POINTER(_D)]),
     "msc_quad_form_grad": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
+    "msc_solve_batched": (_I, [_VP, _I, _VP, ctypes.POINTER(msc_params), _VP]),
 }
 
 
@@ -324,3 +337,56 @@ def solve(ctx: int, op: int, b, sigma, x=None, tol=1e-10, precision=MSC_MIXED, m
     if squeeze:
         x = x[0]
     return x, res
+
+
+def msc_solve_batched(ctx: int, problems, params: msc_params, tuning: msc_tuning | None = None) -> int:
+    """Raw call on a ctypes array of msc_problem; returns the status."""
+    arr = (msc_problem * len(problems))(*problems)
+    return load().msc_solve_batched(ctx, len(problems), ctypes.addressof(arr), ctypes.byref(params),
+                                    ctypes.addressof(tuning) if tuning is not None else None)
+
+
+def solve_batched(ctx: int, items, tol=1e-10, precision=MSC_MIXED, max_iter=100000,
+                  reliable_every=50, freeze=True, refine=4, raise_on_error=True):
+    """Solve many staggered problems together. `items`: list of (op, b, sigma)
+    with b [nrhs][n] complex128 (numpy or torch, host or device). Returns
+    (list of x [nrhs][S][n], list of SolveInfo, msc_tuning)."""
+    probs, keep, outs, infos = [], [], [], []
+    for op, b, sigma in items:
+        sig = np.ascontiguousarray(sigma, dtype=np.float64)
+        S = int(sig.shape[0])
+        if hasattr(b, "data_ptr"):
+            import torch
+            if b.dim() == 1:
+                b = b.unsqueeze(0)
+            b = b.contiguous()
+            nrhs, n = b.shape
+            x = torch.empty((nrhs, S, n), dtype=torch.complex128, device=b.device)
+        else:
+            b = np.ascontiguousarray(b, dtype=np.complex128)
+            if b.ndim == 1:
+                b = b[None, :]
+            nrhs, n = b.shape
+            x = np.empty((nrhs, S, n), dtype=np.complex128)
+        it = np.zeros(nrhs * S, dtype=np.int32)
+        rit = np.zeros(nrhs * S, dtype=np.int32)
+        rho = np.zeros(nrhs * S, dtype=np.float64)
+        info = msc_info()
+        info.shift_iters = it.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        info.shift_refine_iters = rit.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        info.true_rel_resid = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        keep.append((b, sig, it, rit, rho, info))
+        probs.append(msc_problem(op, _ptr(b), nrhs, sig.ctypes.data, S, _ptr(x), ctypes.pointer(info)))
+        outs.append(x)
+    p = msc_params_default()
+    p.tol, p.max_iter, p.precision = float(tol), int(max_iter), int(precision)
+    p.reliable_every, p.freeze_converged, p.refine = int(reliable_every), int(bool(freeze)), int(refine)
+    tun = msc_tuning()
+    st = msc_solve_batched(ctx, probs, p, tun)
+    if st != MSC_OK and raise_on_error and st != MSC_ERR_NOT_CONVERGED:
+        raise MscError(st, "msc_solve_batched")
+    for (b, sig, it, rit, rho, info), x in zip(keep, outs):
+        nrhs = x.shape[0]
+        S = x.shape[1]
+        infos.append(SolveInfo(info, it.reshape(nrhs, S), rit.reshape(nrhs, S), rho.reshape(nrhs, S)))
+    return outs, infos, tun

@@ -54,6 +54,7 @@ struct msc_ctx {
     Buf sys, slot, partial, counter, out_red, descs;
     Buf b64, x64, t64, r, p, t, ps, xit;
     Buf coef, force;  // adjoint: weights c_s and a link-shaped output
+    Buf btab;         // batched solves: system table, operator table, block maps
     int64_t rows_cap = 0;  // rows the desc sections were laid out for
     int gen = 0;
     // pinned host mirrors
@@ -190,8 +191,14 @@ static PassDesc mkdesc(const void* src, const void* aux, const double2* b, void*
     p.sys = sys;
     p.row = row;
     p.fin = fin;
-    p.pad = 0;
+    p.gate = 0;
     return p;
+}
+
+// the same pass, run only in iterations where the system's reliable update is due
+static PassDesc ru_pass(PassDesc d) {
+    d.gate = 1;
+    return d;
 }
 
 static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int out_f32, int sec,
@@ -204,7 +211,9 @@ static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int o
 }
 
 
-// One chunk of `chunk` iterations for `nsys` systems (+ reliable update).
+// One chunk of `chunk` iterations for `nsys` systems. In mixed precision each
+// iteration ends with the reliable-update kernels, which only do work for the
+// systems whose update is due (flag set by the iteration's finalize).
 static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys, int chunk,
                                  bool reliable, bool profile, int64_t npad, int& kernels) {
     Engine e = engine_of(c);
@@ -224,19 +233,19 @@ static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys,
         if (err != cudaSuccess) return err;
         if (prof) cudaEventRecordWithFlags(c->prof[3], c->work, cudaEventRecordExternal);
         kernels += 3;
-    }
-    if (reliable) {
-        cudaError_t err = launch_fold(e, v, nsys, c->work);
-        if (err != cudaSuccess) return err;
-        kernels++;
-        if (A.kind == OP_STAGGERED) {
-            err = op_pass(c, A, PREC_F64, PASS_A, 0, D_RUA, nsys);
+        if (reliable) {
+            err = launch_fold(e, v, nsys, 1, c->work);
+            if (err != cudaSuccess) return err;
+            kernels++;
+            if (A.kind == OP_STAGGERED) {
+                err = op_pass(c, A, PREC_F64, PASS_A, 0, D_RUA, nsys);
+                if (err != cudaSuccess) return err;
+                kernels++;
+            }
+            err = op_pass(c, A, PREC_F64, PASS_C, 1, D_RUC, nsys);
             if (err != cudaSuccess) return err;
             kernels++;
         }
-        err = op_pass(c, A, PREC_F64, PASS_C, 1, D_RUC, nsys);
-        if (err != cudaSuccess) return err;
-        kernels++;
     }
     return cudaSuccess;
 }
@@ -296,7 +305,6 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
         if (!any) break;
         CK(cudaGraphLaunch(ge->exec, c->work));
         c->launches += ge->kernels;
-        if (reliable && rel_updates) (*rel_updates)++;
         CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost,
                            c->work));
         CK(cudaStreamSynchronize(c->work));
@@ -312,12 +320,18 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
             }
         }
     }
+    if (rel_updates)
+        for (int j = 0; j < nsys; ++j) *rel_updates += c->h_sys[j].nru;
     return MSC_OK;
 }
 
 static void init_sys(SysScalars& s, int S, int base, int slot0, int rhs, double d, double tol,
-                     int max_iter, int freeze) {
+                     int max_iter, int freeze, const msc_params& prm) {
     memset(&s, 0, sizeof s);
+    if (prm.precision == MSC_MIXED) {
+        s.ru_every = prm.reliable_every;
+        s.delta2 = prm.reliable_delta * prm.reliable_delta;
+    }
     s.alpha_prev = 1.0;
     s.beta_prev = 0.0;
     s.tol2 = tol * tol;
@@ -368,6 +382,7 @@ void msc_params_default(msc_params* p) {
     p->reliable_every = 50;
     p->freeze_converged = 1;
     p->refine = 4;
+    p->reliable_delta = 0.01;
 }
 
 int msc_create(msc_ctx** out, int device, void* stream) {
@@ -406,7 +421,7 @@ int msc_destroy(msc_ctx* c) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     Buf* bufs[] = {&c->sys, &c->slot, &c->partial, &c->counter, &c->out_red, &c->descs,
                    &c->b64, &c->x64, &c->t64, &c->r, &c->p, &c->t, &c->ps, &c->xit,
-                   &c->coef, &c->force};
+                   &c->coef, &c->force, &c->btab};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_sys) cudaFreeHost(c->h_sys);
@@ -722,7 +737,8 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     if (prm_in) prm = *prm_in;
     if (!(prm.tol > 0) || prm.max_iter < 0 || prm.refine < 0) return MSC_ERR_ARG;
     if (prm.precision != MSC_FP64 && prm.precision != MSC_MIXED) return MSC_ERR_ARG;
-    if (prm.precision == MSC_MIXED && prm.reliable_every < 1) return MSC_ERR_ARG;
+    if (prm.precision == MSC_MIXED && (prm.reliable_every < 1 || !(prm.reliable_delta >= 0.0) ||
+                                       !(prm.reliable_delta < 1.0))) return MSC_ERR_ARG;
     for (int s = 0; s < S; ++s)
         if (!(sigma[s] >= 0.0) || !std::isfinite(sigma[s])) return MSC_ERR_ARG;
     const int prec = prm.precision == MSC_MIXED ? PREC_F32 : PREC_F64;
@@ -758,7 +774,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     const double dstag = A.kind == OP_STAGGERED ? A.mass * A.mass : 0.0;
     const double d0 = dstag + sigma0;
     for (int j = 0; j < nrhs; ++j) {
-        init_sys(c->h_sys[j], S, base, j * S, j, d0, prm.tol, prm.max_iter, prm.freeze_converged);
+        init_sys(c->h_sys[j], S, base, j * S, j, d0, prm.tol, prm.max_iter, prm.freeze_converged, prm);
         for (int s = 0; s < S; ++s) init_slot(c->h_slot[j * S + s], sigma[s] - sigma0);
         const double2* bj = b64 + (size_t)j * npad;
         double2* xb = x64 + (size_t)(j * S + base) * npad;
@@ -770,12 +786,12 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         if (A.kind == OP_STAGGERED) {
             hsec(c, D_K1)[j] = mkdesc(pj, pj, nullptr, tj, d0, j, j, FIN_P);
             hsec(c, D_K2)[j] = mkdesc(tj, pj, nullptr, rj, d0, j, j, FIN_R);
-            hsec(c, D_RUA)[j] = mkdesc(xb, nullptr, nullptr, t64j, 0.0, j, -1, FIN_NONE);
-            hsec(c, D_RUC)[j] = mkdesc(t64j, xb, bj, rj, d0, j, j, FIN_SETR);
+            hsec(c, D_RUA)[j] = ru_pass(mkdesc(xb, nullptr, nullptr, t64j, 0.0, j, -1, FIN_NONE));
+            hsec(c, D_RUC)[j] = ru_pass(mkdesc(t64j, xb, bj, rj, d0, j, j, FIN_SETR));
         } else {
             hsec(c, D_K1)[j] = mkdesc(pj, pj, nullptr, tj, sigma0, j, j, FIN_P);
             hsec(c, D_K2)[j] = mkdesc(nullptr, nullptr, nullptr, nullptr, 0.0, j, j, FIN_R);
-            hsec(c, D_RUC)[j] = mkdesc(xb, xb, bj, rj, sigma0, j, j, FIN_SETR);
+            hsec(c, D_RUC)[j] = ru_pass(mkdesc(xb, xb, bj, rj, sigma0, j, j, FIN_SETR));
         }
     }
     CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * nrhs, cudaMemcpyHostToDevice, c->work));
@@ -785,9 +801,9 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     VecSet v = vecs_of(c, prec, npad);
     CK(launch_init(prec, e, v, dsec(c, D_INIT), nrhs, c->work));
     c->launches++;
-    const int chunk = mixed ? prm.reliable_every : 25;
+    const int chunk = 25;
     ProfAcc pa;
-    int rel = 0;
+    int rel = 0, rel_ref = 0;
     st = run_stage(c, op, prec, nrhs, chunk, mixed, true, npad, prm.max_iter, &pa, &rel);
     if (st) return st;
     int status = MSC_OK;
@@ -801,7 +817,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         else if (s.status == ST_ERR_NONFINITE && status != MSC_ERR_NOT_HPD) status = MSC_ERR_NONFINITE;
     }
     if (mixed) {
-        CK(launch_fold(e, v, nrhs, c->work));
+        CK(launch_fold(e, v, nrhs, 0, c->work));
         c->launches++;
     }
     CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslots, cudaMemcpyDeviceToHost, c->work));
@@ -825,7 +841,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
             for (int k = 0; k < m; ++k) {
                 const int g = todo[k], rhs = g / S, s = g % S;
                 const double dk = dstag + sigma[s];
-                init_sys(c->h_sys[k], 1, 0, g, rhs, dk, 0.5 * prm.tol, prm.max_iter, 1);
+                init_sys(c->h_sys[k], 1, 0, g, rhs, dk, 0.5 * prm.tol, prm.max_iter, 1, prm);
                 c->h_sys[k].tol2_acc = prm.tol * prm.tol;
                 c->h_sys[k].bnorm2 = bnorm2[rhs];
                 init_slot(c->h_slot[g], 0.0);
@@ -840,13 +856,13 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
                     hsec(c, D_RIC)[k] = mkdesc(t64k, xg, bj, rk, dk, k, k, FIN_SETR_INIT);
                     hsec(c, D_K1)[k] = mkdesc(pk, pk, nullptr, tk, dk, k, k, FIN_P);
                     hsec(c, D_K2)[k] = mkdesc(tk, pk, nullptr, rk, dk, k, k, FIN_R);
-                    hsec(c, D_RUA)[k] = mkdesc(xg, nullptr, nullptr, t64k, 0.0, k, -1, FIN_NONE);
-                    hsec(c, D_RUC)[k] = mkdesc(t64k, xg, bj, rk, dk, k, k, FIN_SETR);
+                    hsec(c, D_RUA)[k] = ru_pass(mkdesc(xg, nullptr, nullptr, t64k, 0.0, k, -1, FIN_NONE));
+                    hsec(c, D_RUC)[k] = ru_pass(mkdesc(t64k, xg, bj, rk, dk, k, k, FIN_SETR));
                 } else {
                     hsec(c, D_RIC)[k] = mkdesc(xg, xg, bj, rk, sigma[s], k, k, FIN_SETR_INIT);
                     hsec(c, D_K1)[k] = mkdesc(pk, pk, nullptr, tk, sigma[s], k, k, FIN_P);
                     hsec(c, D_K2)[k] = mkdesc(nullptr, nullptr, nullptr, nullptr, 0.0, k, k, FIN_R);
-                    hsec(c, D_RUC)[k] = mkdesc(xg, xg, bj, rk, sigma[s], k, k, FIN_SETR);
+                    hsec(c, D_RUC)[k] = ru_pass(mkdesc(xg, xg, bj, rk, sigma[s], k, k, FIN_SETR));
                 }
             }
             CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * m, cudaMemcpyHostToDevice, c->work));
@@ -868,7 +884,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
             if (check_only || next.empty() || status != MSC_OK) break;
             CK(launch_init_from_r(prec, e, v, m, c->work));
             c->launches++;
-            st = run_stage(c, op, prec, m, chunk, mixed, false, npad, prm.max_iter, nullptr, &rel);
+            st = run_stage(c, op, prec, m, chunk, mixed, false, npad, prm.max_iter, nullptr, &rel_ref);
             if (st) return st;
             int most = 0;
             for (int k = 0; k < m; ++k) {
@@ -881,7 +897,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
             ref_total += most;
             rounds++;
             if (mixed) {
-                CK(launch_fold(e, v, m, c->work));
+                CK(launch_fold(e, v, m, 0, c->work));
                 c->launches++;
             }
             if (status != MSC_OK) break;
@@ -900,7 +916,8 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         info->iters = iters;
         info->refine_rounds = rounds;
         info->refine_iters = ref_total;
-        info->reliable_updates = rel;
+        info->reliable_updates = rel + rel_ref;
+        info->refine_reliable_updates = rel_ref;
         info->kernel_launches = (int)(c->launches - launches0);
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int g = 0; g < nslots; ++g) {
@@ -917,6 +934,554 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched uneven systems
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchShape {
+    int site_threads = 128;
+    int vec_threads = 256;
+    int units = 4;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<BatchShape, double>> g_tune_cache;
+
+// Device-side tables of one stage of a batched solve.
+struct BatchDev {
+    BSys* sys = nullptr;
+    BOp* ops = nullptr;
+    int* msite = nullptr;  // blocks of the operator passes
+    int* mvec = nullptr;   // one unit per thread (init, fold)
+    int* mupd = nullptr;   // `units` units per thread (update)
+    int nsite = 0, nvec = 0, nupd = 0;
+};
+
+}  // namespace
+
+static int64_t pad64(int64_t n) { return (n + 63) / 64 * 64; }
+
+// Prefix-sum block maps of the systems for one launch shape; uploads the
+// system and operator tables with them (into c->btab).
+static int upload_batch_tables(msc_ctx* c, const std::vector<BSys>& sys, const std::vector<BOp>& ops,
+                               const BatchShape& sh, int prec, BatchDev& bd) {
+    const int J = (int)sys.size();
+    const int cpu = prec == PREC_F32 ? 2 : 1;
+    std::vector<int> ms(J + 1), mv(J + 1), mu(J + 1);
+    int64_t a = 0, b = 0, u = 0;
+    for (int j = 0; j < J; ++j) {
+        ms[j] = (int)a;
+        mv[j] = (int)b;
+        mu[j] = (int)u;
+        const int V = ops[sys[j].op].g.V;
+        const int64_t upv = sys[j].npad / cpu;
+        a += (V + sh.site_threads - 1) / sh.site_threads;
+        b += (upv + sh.vec_threads - 1) / sh.vec_threads;
+        u += (upv + (int64_t)sh.vec_threads * sh.units - 1) / ((int64_t)sh.vec_threads * sh.units);
+        if (a >= ((int64_t)1 << 30) || b >= ((int64_t)1 << 30)) return MSC_ERR_UNSUPPORTED;
+        if ((a - ms[j]) > kMaxBlocks || (b - mv[j]) > kMaxBlocks) return MSC_ERR_UNSUPPORTED;
+    }
+    ms[J] = (int)a;
+    mv[J] = (int)b;
+    mu[J] = (int)u;
+    const size_t bsys = sizeof(BSys) * J, bops = sizeof(BOp) * ops.size(), bmap = sizeof(int) * (J + 1);
+    const size_t off_ops = (bsys + 255) / 256 * 256;
+    const size_t off_ms = off_ops + (bops + 255) / 256 * 256;
+    const size_t off_mv = off_ms + (bmap + 255) / 256 * 256;
+    const size_t off_mu = off_mv + (bmap + 255) / 256 * 256;
+    const size_t total = off_mu + bmap;
+    bool moved = false;
+    CK(grow(c->btab, total, moved));
+    if (moved) c->gen++;
+    char* base = (char*)c->btab.p;
+    CK(cudaMemcpyAsync(base, sys.data(), bsys, cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpyAsync(base + off_ops, ops.data(), bops, cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpyAsync(base + off_ms, ms.data(), bmap, cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpyAsync(base + off_mv, mv.data(), bmap, cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpyAsync(base + off_mu, mu.data(), bmap, cudaMemcpyHostToDevice, c->work));
+    // the host vectors above are pageable: wait before they go out of scope
+    CK(cudaStreamSynchronize(c->work));
+    bd.sys = (BSys*)base;
+    bd.ops = (BOp*)(base + off_ops);
+    bd.msite = (int*)(base + off_ms);
+    bd.mvec = (int*)(base + off_mv);
+    bd.mupd = (int*)(base + off_mu);
+    bd.nsite = (int)a;
+    bd.nvec = (int)b;
+    bd.nupd = (int)u;
+    return MSC_OK;
+}
+
+static BVec bvec_of(msc_ctx* c, int prec) {
+    BVec v;
+    v.r = c->r.p;
+    v.p = c->p.p;
+    v.t = c->t.p;
+    v.ps = c->ps.p;
+    v.xit = prec == PREC_F32 ? c->xit.p : c->x64.p;
+    v.x64 = (double2*)c->x64.p;
+    v.t64 = (double2*)c->t64.p;
+    v.b64 = (const double2*)c->b64.p;
+    return v;
+}
+
+static cudaError_t enqueue_chunk_b(msc_ctx* c, int prec, int J, int chunk, bool reliable,
+                                   const BatchDev& bd, const BatchShape& sh, int& kernels) {
+    Engine e = engine_of(c);
+    BVec v = bvec_of(c, prec);
+    kernels = 0;
+    cudaError_t err = cudaSuccess;
+    for (int it = 0; it < chunk && err == cudaSuccess; ++it) {
+        err = launch_b_stag(prec, PASS_A, 0, e, dsec(c, D_K1), bd.sys, bd.ops, bd.msite, J, bd.nsite,
+                            sh.site_threads, c->work);
+        if (err == cudaSuccess)
+            err = launch_b_stag(prec, PASS_B, 0, e, dsec(c, D_K2), bd.sys, bd.ops, bd.msite, J, bd.nsite,
+                                sh.site_threads, c->work);
+        if (err == cudaSuccess)
+            err = launch_b_update(prec, sh.units, e, v, bd.sys, bd.mupd, J, bd.nupd, sh.vec_threads, c->work);
+        kernels += 3;
+        if (reliable && err == cudaSuccess) {
+            err = launch_b_fold(e, v, bd.sys, bd.mvec, J, bd.nvec, sh.vec_threads, 1, c->work);
+            if (err == cudaSuccess)
+                err = launch_b_stag(PREC_F64, PASS_A, 0, e, dsec(c, D_RUA), bd.sys, bd.ops, bd.msite, J,
+                                    bd.nsite, sh.site_threads, c->work);
+            if (err == cudaSuccess)
+                err = launch_b_stag(PREC_F64, PASS_C, 1, e, dsec(c, D_RUC), bd.sys, bd.ops, bd.msite, J,
+                                    bd.nsite, sh.site_threads, c->work);
+            kernels += 3;
+        }
+    }
+    return err;
+}
+
+static int run_stage_b(msc_ctx* c, int prec, int J, int chunk, bool reliable, const BatchDev& bd,
+                       const BatchShape& sh, int max_iter, int* rel_updates) {
+    char key[200];
+    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d", prec, J, chunk, (int)reliable, bd.nsite,
+             bd.nvec, bd.nupd, sh.site_threads, sh.vec_threads, sh.units, c->gen);
+    GraphEntry& ge = c->graphs[key];
+    if (!ge.exec || ge.gen != c->gen) {
+        if (ge.exec) cudaGraphExecDestroy(ge.exec);
+        ge.exec = nullptr;
+        CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
+        int kernels = 0;
+        cudaError_t err = enqueue_chunk_b(c, prec, J, chunk, reliable, bd, sh, kernels);
+        cudaGraph_t g = nullptr;
+        cudaError_t err2 = cudaStreamEndCapture(c->work, &g);
+        if (err != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_status(err); }
+        if (err2 != cudaSuccess) return cuda_status(err2);
+        err = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (err != cudaSuccess) return cuda_status(err);
+        ge.gen = c->gen;
+        ge.kernels = kernels;
+    }
+    CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * J, cudaMemcpyDeviceToHost, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    const long max_chunks = (long)max_iter / chunk + 2;
+    for (long k = 0; k < max_chunks; ++k) {
+        bool any = false;
+        for (int j = 0; j < J; ++j)
+            if (c->h_sys[j].status < ST_DONE) any = true;
+        if (!any) break;
+        CK(cudaGraphLaunch(ge.exec, c->work));
+        c->launches += ge.kernels;
+        CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * J, cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+    }
+    if (rel_updates)
+        for (int j = 0; j < J; ++j) *rel_updates += c->h_sys[j].nru;
+    return MSC_OK;
+}
+
+// Times candidate launch shapes on the batch (operator pass + update, with
+// reductions that finalise nothing) and returns the fastest. Runs before the
+// solve initialises its vectors, on whatever they hold.
+static int autotune_batch(msc_ctx* c, int prec, const std::vector<BSys>& sys, const std::vector<BOp>& ops,
+                          int nslots, BatchShape& best, double& best_ms) {
+    const int J = (int)sys.size();
+    Engine e = engine_of(c);
+    BVec v = bvec_of(c, prec);
+    std::vector<PassDesc> keep(hsec(c, D_K1), hsec(c, D_K1) + J);
+    for (int j = 0; j < J; ++j) hsec(c, D_K1)[j].fin = FIN_NONE;
+    CK(upload_sec(c, D_K1, J));
+    for (int g = 0; g < nslots; ++g) c->h_slot[g].flag = 2;
+    CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * J, cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
+    const int site_c[] = {64, 128, 256};
+    const int vec_c[][2] = {{256, 1}, {256, 2}, {256, 4}, {128, 4}};
+    cudaEvent_t e0 = c->prof[0], e1 = c->prof[1];
+    best_ms = 1e30;
+    int st = MSC_OK;
+    for (int si : site_c) {
+        for (auto& vc : vec_c) {
+            BatchShape sh;
+            sh.site_threads = si;
+            sh.vec_threads = vc[0];
+            sh.units = vc[1];
+            BatchDev bd;
+            st = upload_batch_tables(c, sys, ops, sh, prec, bd);
+            if (st == MSC_ERR_UNSUPPORTED) continue;  // a system needs more blocks than a row holds
+            if (st) return st;
+            float ms = 0;
+            for (int rep = 0; rep < 4; ++rep) {
+                if (rep == 1) CK(cudaEventRecord(e0, c->work));
+                CK(launch_b_stag(prec, PASS_A, 0, e, dsec(c, D_K1), bd.sys, bd.ops, bd.msite, J, bd.nsite,
+                                 sh.site_threads, c->work));
+                CK(launch_b_update(prec, sh.units, e, v, bd.sys, bd.mupd, J, bd.nupd, sh.vec_threads, c->work));
+            }
+            CK(cudaEventRecord(e1, c->work));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= 3.0f;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = sh;
+            }
+        }
+    }
+    for (int j = 0; j < J; ++j) hsec(c, D_K1)[j] = keep[j];
+    for (int g = 0; g < nslots; ++g) c->h_slot[g].flag = 0;
+    return best_ms < 1e30 ? MSC_OK : MSC_ERR_UNSUPPORTED;
+}
+
+extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs, const msc_params* prm_in,
+                                 msc_tuning* tuning) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || nprob <= 0 || !probs) return MSC_ERR_ARG;
+    msc_params prm;
+    msc_params_default(&prm);
+    if (prm_in) prm = *prm_in;
+    if (!(prm.tol > 0) || prm.max_iter < 0 || prm.refine < 0) return MSC_ERR_ARG;
+    if (prm.precision != MSC_FP64 && prm.precision != MSC_MIXED) return MSC_ERR_ARG;
+    if (prm.precision == MSC_MIXED && (prm.reliable_every < 1 || !(prm.reliable_delta >= 0.0) ||
+                                       !(prm.reliable_delta < 1.0))) return MSC_ERR_ARG;
+    for (int i = 0; i < nprob; ++i) {
+        const msc_problem& q = probs[i];
+        if (!q.op || q.op->ctx != c || q.op->dev.kind != OP_STAGGERED || !q.b || !q.x || !q.sigma) return MSC_ERR_ARG;
+        if (q.nrhs <= 0 || q.S <= 0 || q.S > kMaxShifts) return MSC_ERR_ARG;
+        for (int s = 0; s < q.S; ++s)
+            if (!(q.sigma[s] >= 0.0) || !std::isfinite(q.sigma[s])) return MSC_ERR_ARG;
+    }
+    const int prec = prm.precision == MSC_MIXED ? PREC_F32 : PREC_F64;
+    const bool mixed = prec == PREC_F32;
+    const size_t elem = mixed ? 8 : 16;
+    int st = begin(c);
+    if (st) return st;
+    const long launches0 = c->launches;
+    // ---- layout: one system per (problem, right-hand side) ------------------
+    std::vector<BOp> ops(nprob);
+    std::vector<BSys> sys;
+    std::vector<int> sys_prob, sys_rhs, slot_sys, slot_shift;
+    int64_t VR = 0, VS = 0;
+    for (int i = 0; i < nprob; ++i) {
+        const OpDev& A = probs[i].op->dev;
+        ops[i].g = A.g;
+        ops[i].nc = A.nc;
+        ops[i].recon = A.recon;
+        ops[i].l32 = A.links32;
+        ops[i].l64 = A.links64;
+        const int64_t np = pad64(A.n);
+        for (int r = 0; r < probs[i].nrhs; ++r) {
+            BSys q;
+            q.voff = VR;
+            q.soff = VS;
+            q.boff = VR;
+            q.npad = (int)np;
+            q.op = i;
+            for (int s = 0; s < probs[i].S; ++s) {
+                slot_sys.push_back((int)sys.size());
+                slot_shift.push_back(s);
+            }
+            sys.push_back(q);
+            sys_prob.push_back(i);
+            sys_rhs.push_back(r);
+            VR += np;
+            VS += np * probs[i].S;
+        }
+    }
+    const int J = (int)sys.size();
+    const int nslots = (int)slot_sys.size();
+    std::vector<int64_t> slot_off(nslots);
+    for (int g = 0; g < nslots; ++g) slot_off[g] = sys[slot_sys[g]].soff + (int64_t)slot_shift[g] * sys[slot_sys[g]].npad;
+    // ---- workspace -----------------------------------------------------------
+    {
+        bool moved = false;
+        const int64_t rows = std::max(J, nslots);
+        if (rows > c->rows_cap) {
+            c->rows_cap = rows;
+            moved = true;
+        }
+        const int64_t R = std::max<int64_t>(c->rows_cap, 3);
+        c->rows_cap = R;
+        const int64_t VM = std::max(VR, VS);
+        CK(grow(c->sys, sizeof(SysScalars) * R, moved));
+        CK(grow(c->slot, sizeof(SlotScalars) * R, moved));
+        CK(grow(c->partial, sizeof(double) * kMaxBlocks * R, moved));
+        CK(grow(c->counter, sizeof(unsigned) * R, moved));
+        CK(grow(c->out_red, sizeof(double) * R, moved));
+        CK(grow(c->descs, sizeof(PassDesc) * D_NSECT * R, moved));
+        CK(grow(c->b64, (size_t)VR * 16, moved));
+        CK(grow(c->x64, (size_t)VS * 16, moved));
+        CK(grow(c->t64, (size_t)VM * 16, moved));
+        CK(grow(c->r, (size_t)VM * elem, moved));
+        CK(grow(c->p, (size_t)VM * elem, moved));
+        CK(grow(c->t, (size_t)VM * elem, moved));
+        CK(grow(c->ps, (size_t)VS * elem, moved));
+        CK(grow(c->xit, (size_t)VS * 8, moved));
+        if (moved) c->gen++;
+        if (R > c->h_rows || R > c->h_slots) {
+            if (c->h_sys) cudaFreeHost(c->h_sys);
+            if (c->h_slot) cudaFreeHost(c->h_slot);
+            if (c->h_red) cudaFreeHost(c->h_red);
+            if (c->h_desc) cudaFreeHost(c->h_desc);
+            CK(cudaMallocHost((void**)&c->h_sys, sizeof(SysScalars) * R));
+            CK(cudaMallocHost((void**)&c->h_slot, sizeof(SlotScalars) * R));
+            CK(cudaMallocHost((void**)&c->h_red, sizeof(double) * R));
+            CK(cudaMallocHost((void**)&c->h_desc, sizeof(PassDesc) * D_NSECT * R));
+            c->h_rows = R;
+            c->h_slots = R;
+        }
+        // padding of every row must read as zero
+        CK(cudaMemsetAsync(c->b64.p, 0, (size_t)VR * 16, c->work));
+        CK(cudaMemsetAsync(c->r.p, 0, (size_t)VM * elem, c->work));
+        CK(cudaMemsetAsync(c->t.p, 0, (size_t)VM * elem, c->work));
+    }
+    char* r = (char*)c->r.p;
+    char* p = (char*)c->p.p;
+    char* t = (char*)c->t.p;
+    double2* x64 = (double2*)c->x64.p;
+    double2* t64 = (double2*)c->t64.p;
+    double2* b64 = (double2*)c->b64.p;
+    for (int j = 0; j < J; ++j) {
+        const msc_problem& q = probs[sys_prob[j]];
+        const int64_t n = q.op->dev.n;
+        CK(cudaMemcpyAsync(b64 + sys[j].boff, q.b + (size_t)sys_rhs[j] * n * 2, n * 16, cudaMemcpyDefault, c->work));
+    }
+    // ---- scalars and pass descriptors of the multi-shift stage ---------------
+    std::vector<double> d0(J);
+    int slot0 = 0;
+    for (int j = 0; j < J; ++j) {
+        const msc_problem& q = probs[sys_prob[j]];
+        const OpDev& A = q.op->dev;
+        int base = 0;
+        for (int s = 1; s < q.S; ++s)
+            if (q.sigma[s] < q.sigma[base]) base = s;
+        d0[j] = A.mass * A.mass + q.sigma[base];
+        init_sys(c->h_sys[j], q.S, base, slot0, j, d0[j], prm.tol, prm.max_iter, prm.freeze_converged, prm);
+        for (int s = 0; s < q.S; ++s) init_slot(c->h_slot[slot0 + s], q.sigma[s] - q.sigma[base]);
+        void* rj = r + sys[j].voff * elem;
+        void* pj = p + sys[j].voff * elem;
+        void* tj = t + sys[j].voff * elem;
+        double2* t64j = t64 + sys[j].voff;
+        double2* xb = x64 + sys[j].soff + (int64_t)base * sys[j].npad;
+        const double2* bj = b64 + sys[j].boff;
+        hsec(c, D_K1)[j] = mkdesc(pj, pj, nullptr, tj, d0[j], j, j, FIN_P);
+        hsec(c, D_K2)[j] = mkdesc(tj, pj, nullptr, rj, d0[j], j, j, FIN_R);
+        hsec(c, D_RUA)[j] = ru_pass(mkdesc(xb, nullptr, nullptr, t64j, 0.0, j, -1, FIN_NONE));
+        hsec(c, D_RUC)[j] = ru_pass(mkdesc(t64j, xb, bj, rj, d0[j], j, j, FIN_SETR));
+        slot0 += q.S;
+    }
+    // ---- autotuned launch shape ------------------------------------------------
+    BatchShape shape;
+    double tuned_ms = 0.0;
+    int tuned_now = 0;
+    {
+        int64_t sumV = 0;
+        for (auto& q : sys) sumV += ops[q.op].g.V;
+        char key[160];
+        int dev = 0;
+        cudaGetDevice(&dev);
+        snprintf(key, sizeof key, "%d|%d|%d|%lld|%d", dev, prec, J, (long long)sumV, nslots);
+        std::pair<BatchShape, double> hit;
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                hit = it->second;
+                found = true;
+            }
+        }
+        if (found) {
+            shape = hit.first;
+            tuned_ms = hit.second;
+        } else {
+            st = autotune_batch(c, prec, sys, ops, nslots, shape, tuned_ms);
+            if (st) return st;
+            tuned_now = 1;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[key] = {shape, tuned_ms};
+        }
+    }
+    if (tuning) {
+        tuning->site_threads = shape.site_threads;
+        tuning->vec_threads = shape.vec_threads;
+        tuning->vec_units = shape.units;
+        tuning->tuned = tuned_now;
+        tuning->best_ms = tuned_ms;
+    }
+    CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * J, cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
+    for (int sct : {D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, sct, J));
+    BatchDev bd;
+    st = upload_batch_tables(c, sys, ops, shape, prec, bd);
+    if (st) return st;
+    Engine e = engine_of(c);
+    BVec v = bvec_of(c, prec);
+    CK(launch_b_init(prec, e, v, bd.sys, bd.mvec, J, bd.nvec, shape.vec_threads, c->work));
+    c->launches++;
+    const int chunk = 25;
+    int rel = 0, rel_ref = 0;
+    st = run_stage_b(c, prec, J, chunk, mixed, bd, shape, prm.max_iter, &rel);
+    if (st) return st;
+    std::vector<int> sys_status(J, MSC_OK), sys_iters(J, 0);
+    std::vector<double> bnorm2(J);
+    for (int j = 0; j < J; ++j) {
+        const SysScalars& q = c->h_sys[j];
+        sys_iters[j] = q.it;
+        bnorm2[j] = q.bnorm2;
+        if (q.status == ST_ERR_NOT_HPD) sys_status[j] = MSC_ERR_NOT_HPD;
+        else if (q.status == ST_ERR_NONFINITE) sys_status[j] = MSC_ERR_NONFINITE;
+    }
+    if (mixed) {
+        CK(launch_b_fold(e, v, bd.sys, bd.mvec, J, bd.nvec, shape.vec_threads, 0, c->work));
+        c->launches++;
+    }
+    CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslots, cudaMemcpyDeviceToHost, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    std::vector<int> shift_iters(nslots), ref_iters(nslots, 0);
+    for (int g = 0; g < nslots; ++g) shift_iters[g] = c->h_slot[g].conv_iter;
+    // ---- true residuals and refinement (one system per refined shift) --------
+    std::vector<double> rho(nslots, std::nan(""));
+    int rounds = 0, ref_total = 0;
+    std::vector<int> todo;
+    for (int g = 0; g < nslots; ++g)
+        if (sys_status[slot_sys[g]] == MSC_OK) todo.push_back(g);
+    for (int round = 0; !todo.empty(); ++round) {
+        const bool check_only = round >= prm.refine;
+        const int m = (int)todo.size();
+        std::vector<BSys> rs(m);
+        int64_t voff = 0;
+        for (int k = 0; k < m; ++k) {
+            const int g = todo[k], j = slot_sys[g], s = slot_shift[g];
+            const msc_problem& q = probs[sys_prob[j]];
+            const double dk = q.op->dev.mass * q.op->dev.mass + q.sigma[s];
+            rs[k] = sys[j];
+            rs[k].voff = voff;
+            rs[k].soff = slot_off[g];
+            voff += sys[j].npad;
+            init_sys(c->h_sys[k], 1, 0, g, j, dk, 0.5 * prm.tol, prm.max_iter, 1, prm);
+            c->h_sys[k].tol2_acc = prm.tol * prm.tol;
+            c->h_sys[k].bnorm2 = bnorm2[j];
+            init_slot(c->h_slot[g], 0.0);
+            void* rk = r + rs[k].voff * elem;
+            void* pk = p + rs[k].voff * elem;
+            void* tk = t + rs[k].voff * elem;
+            double2* t64k = t64 + rs[k].voff;
+            double2* xg = x64 + slot_off[g];
+            const double2* bj = b64 + sys[j].boff;
+            hsec(c, D_RIA)[k] = mkdesc(xg, nullptr, nullptr, t64k, 0.0, k, -1, FIN_NONE);
+            hsec(c, D_RIC)[k] = mkdesc(t64k, xg, bj, rk, dk, k, k, FIN_SETR_INIT);
+            hsec(c, D_K1)[k] = mkdesc(pk, pk, nullptr, tk, dk, k, k, FIN_P);
+            hsec(c, D_K2)[k] = mkdesc(tk, pk, nullptr, rk, dk, k, k, FIN_R);
+            hsec(c, D_RUA)[k] = ru_pass(mkdesc(xg, nullptr, nullptr, t64k, 0.0, k, -1, FIN_NONE));
+            hsec(c, D_RUC)[k] = ru_pass(mkdesc(t64k, xg, bj, rk, dk, k, k, FIN_SETR));
+        }
+        CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * m, cudaMemcpyHostToDevice, c->work));
+        CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
+        for (int sct : {D_RIA, D_RIC, D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, sct, m));
+        BatchDev rd;
+        st = upload_batch_tables(c, rs, ops, shape, prec, rd);
+        if (st) return st;
+        CK(launch_b_stag(PREC_F64, PASS_A, 0, e, dsec(c, D_RIA), rd.sys, rd.ops, rd.msite, m, rd.nsite,
+                         shape.site_threads, c->work));
+        CK(launch_b_stag(PREC_F64, PASS_C, mixed ? 1 : 0, e, dsec(c, D_RIC), rd.sys, rd.ops, rd.msite, m,
+                         rd.nsite, shape.site_threads, c->work));
+        c->launches += 2;
+        CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * m, cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        std::vector<int> next;
+        for (int k = 0; k < m; ++k) {
+            const SysScalars& q = c->h_sys[k];
+            const int g = todo[k], j = slot_sys[g];
+            rho[g] = bnorm2[j] > 0 ? std::sqrt(q.R / bnorm2[j]) : 0.0;
+            if (q.status == ST_ERR_NONFINITE) sys_status[j] = MSC_ERR_NONFINITE;
+            else if (q.status == ST_RUNNING) next.push_back(g);
+        }
+        if (check_only || next.empty()) break;
+        CK(launch_b_init_from_r(prec, e, v, rd.sys, rd.mvec, m, rd.nvec, shape.vec_threads, c->work));
+        c->launches++;
+        st = run_stage_b(c, prec, m, chunk, mixed, rd, shape, prm.max_iter, &rel_ref);
+        if (st) return st;
+        int most = 0;
+        for (int k = 0; k < m; ++k) {
+            const SysScalars& q = c->h_sys[k];
+            const int g = todo[k], j = slot_sys[g];
+            ref_iters[g] += q.it;
+            most = std::max(most, q.it);
+            if (q.status == ST_ERR_NOT_HPD) sys_status[j] = MSC_ERR_NOT_HPD;
+            else if (q.status == ST_ERR_NONFINITE) sys_status[j] = MSC_ERR_NONFINITE;
+        }
+        ref_total += most;
+        rounds++;
+        if (mixed) {
+            CK(launch_b_fold(e, v, rd.sys, rd.mvec, m, rd.nvec, shape.vec_threads, 0, c->work));
+            c->launches++;
+        }
+        todo.clear();
+        for (int g : next)
+            if (sys_status[slot_sys[g]] == MSC_OK) todo.push_back(g);
+    }
+    // ---- solutions out, reports ------------------------------------------------
+    for (int j = 0; j < J; ++j) {
+        const msc_problem& q = probs[sys_prob[j]];
+        const int64_t n = q.op->dev.n;
+        CK(cudaMemcpy2DAsync(q.x + (size_t)sys_rhs[j] * q.S * n * 2, n * 16, x64 + sys[j].soff, (size_t)sys[j].npad * 16,
+                             n * 16, q.S, cudaMemcpyDefault, c->work));
+    }
+    CK(cudaStreamSynchronize(c->work));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int worst = MSC_OK;
+    int gfirst = 0;
+    int jfirst = 0;
+    for (int i = 0; i < nprob; ++i) {
+        const msc_problem& q = probs[i];
+        int pst = MSC_OK, iters = 0;
+        for (int rr = 0; rr < q.nrhs; ++rr) {
+            const int j = jfirst + rr;
+            iters = std::max(iters, sys_iters[j]);
+            if (sys_status[j] != MSC_OK && pst == MSC_OK) pst = sys_status[j];
+        }
+        if (pst == MSC_OK)
+            for (int g = gfirst; g < gfirst + q.nrhs * q.S; ++g)
+                if (!(rho[g] <= prm.tol)) pst = MSC_ERR_NOT_CONVERGED;
+        if (q.info) {
+            msc_info* in = q.info;
+            in->status = pst;
+            in->iters = iters;
+            in->refine_rounds = rounds;
+            in->refine_iters = ref_total;
+            in->reliable_updates = rel + rel_ref;
+            in->refine_reliable_updates = rel_ref;
+            in->kernel_launches = (int)(c->launches - launches0);
+            in->seconds = secs;
+            for (int k = 0; k < q.nrhs * q.S; ++k) {
+                if (in->shift_iters) in->shift_iters[k] = shift_iters[gfirst + k];
+                if (in->shift_refine_iters) in->shift_refine_iters[k] = ref_iters[gfirst + k];
+                if (in->true_rel_resid) in->true_rel_resid[k] = rho[gfirst + k];
+            }
+            in->op_ms = in->rupdate_ms = in->update_ms = 0.0;
+            in->prof_samples = 0;
+        }
+        if (pst != MSC_OK && (worst == MSC_OK || worst == MSC_ERR_NOT_CONVERGED)) worst = pst;
+        gfirst += q.nrhs * q.S;
+        jfirst += q.nrhs;
+    }
+    return worst;
+}
 
 // ---------------------------------------------------------------------------
 // Adjoint of S = sum_s c_s Re(phi^dag x_s) (rational pseudofermion action)

@@ -12,29 +12,6 @@
 
 namespace msc {
 
-template <class T> struct U16;
-template <> struct U16<float> { using t = float4; static constexpr int cpu = 2; };
-template <> struct U16<double> { using t = double2; static constexpr int cpu = 1; };
-
-__device__ __forceinline__ float4 axpy(float a, float4 x, float4 y) {
-    return {fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w)};
-}
-__device__ __forceinline__ double2 axpy(double a, double2 x, double2 y) {
-    return {fma(a, x.x, y.x), fma(a, x.y, y.y)};
-}
-// a*x + b*y
-__device__ __forceinline__ float4 axpby(float a, float4 x, float b, float4 y) {
-    return {fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z), fmaf(a, x.w, b * y.w)};
-}
-__device__ __forceinline__ double2 axpby(double a, double2 x, double b, double2 y) {
-    return {fma(a, x.x, b * y.x), fma(a, x.y, b * y.y)};
-}
-__device__ __forceinline__ float sq(float4 v) { return v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w; }
-__device__ __forceinline__ double sq(double2 v) { return v.x * v.x + v.y * v.y; }
-__device__ __forceinline__ float4 to_unit(double2 a, double2 b) {
-    return {(float)a.x, (float)a.y, (float)b.x, (float)b.y};
-}
-
 // r = b (in iteration precision), p = r, p_s = r (non-base shifts), x = 0;
 // reduction |b|^2 in FP64 from the FP64 source.
 template <class T>
@@ -237,11 +214,12 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, cons
 
 // x_s(FP64) += x_s(FP32 accumulator); accumulator = 0, for every shift of
 // the system (mixed precision; runs whatever the system's status).
-__global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v) {
+__global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v, int only_ru) {
     const int j = blockIdx.y;
     const SysScalars* s = &e.sys[j];
     const int st = load_status(s);
     if (st == ST_ERR_NOT_HPD || st == ST_ERR_NONFINITE) return;
+    if (only_ru && (st != ST_RUNNING || __ldcg(&s->ru) == 0)) return;
     const int S = s->S, slot0 = s->slot0;
     const int64_t upv = v.npad / 2;
     float4* xa = (float4*)v.xit;
@@ -342,8 +320,8 @@ cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const P
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, cudaStream_t st) {
-    k_fold<<<vgrid(k_fold, v.npad / 2, 1, nsys), kThreads, 0, st>>>(e, v);
+cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int only_ru, cudaStream_t st) {
+    k_fold<<<vgrid(k_fold, v.npad / 2, 1, nsys), kThreads, 0, st>>>(e, v, only_ru);
     return cudaGetLastError();
 }
 

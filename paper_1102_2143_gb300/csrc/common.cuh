@@ -56,9 +56,16 @@ struct SysScalars {
     double tol2;      // tol^2
     double d;         // diagonal shift of the operator pass (m^2+sigma0 or sigma0)
     double tol2_acc;  // start-of-solve acceptance: done at once if R <= tol2_acc |b|^2
+    double Rmax;      // largest iterated R since the last reliable update
+    double delta2;    // reliable update once R <= delta2 * Rmax
     int status, it, max_iter, capped;
     int S, base, slot0, rhs;
-    int freeze, pad0, pad1, pad2;
+    int freeze;
+    int ru_every;     // reliable update at the latest after this many iterations (0: never)
+    int since_ru;     // iterations since the last reliable update
+    int ru;           // 1: the reliable-update kernels of this iteration run
+    int nru;          // reliable updates done
+    int pad0;
 };
 
 struct SlotScalars {
@@ -82,7 +89,8 @@ struct PassDesc {
     int sys;            // gating system (-1: always run)
     int row;            // reduction row (-1: no reduction)
     int fin;            // FIN_*
-    int pad;
+    int gate;           // 0: run while the system iterates; 1: also only when its
+                        //    reliable update is due
 };
 
 struct Engine {
@@ -156,23 +164,25 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Publishes this block's sum of v to row `row`; returns true in every thread
-// of the last block to arrive, with the fixed-order total in `total`.
-__device__ __forceinline__ bool reduce_last(const Engine& e, int row, double v, double& total) {
+// of the last of the `nblocks` blocks that reduce into that row to arrive
+// (`bidx` = this block's index among them), with the fixed-order total.
+__device__ __forceinline__ bool reduce_last_n(const Engine& e, int row, double v, double& total,
+                                              int nblocks, int bidx) {
     __shared__ double sh[32];
     __shared__ int is_last;
     __shared__ double tot;
     double bs = block_sum(v, sh);
     if (threadIdx.x == 0) {
-        e.partial[(size_t)row * kMaxBlocks + blockIdx.x] = bs;
+        e.partial[(size_t)row * kMaxBlocks + bidx] = bs;
         __threadfence();
         unsigned t = atomicAdd(&e.counter[row], 1u);
-        is_last = (t == gridDim.x - 1);
+        is_last = (t == (unsigned)nblocks - 1);
     }
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
     double acc = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x)
         acc += __ldcg(&e.partial[(size_t)row * kMaxBlocks + i]);
     double s = block_sum(acc, sh);
     if (threadIdx.x == 0) {
@@ -184,18 +194,52 @@ __device__ __forceinline__ bool reduce_last(const Engine& e, int row, double v, 
     return true;
 }
 
+__device__ __forceinline__ bool reduce_last(const Engine& e, int row, double v, double& total) {
+    return reduce_last_n(e, row, v, total, (int)gridDim.x, (int)blockIdx.x);
+}
+
 // Last block only: signals that every block of a non-reducing kernel is done.
-__device__ __forceinline__ bool arrive_last(const Engine& e, int row) {
+__device__ __forceinline__ bool arrive_last_n(const Engine& e, int row, int nblocks) {
     __shared__ int is_last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         unsigned t = atomicAdd(&e.counter[row], 1u);
-        is_last = (t == gridDim.x - 1);
+        is_last = (t == (unsigned)nblocks - 1);
         if (is_last) e.counter[row] = 0u;
     }
     __syncthreads();
     return is_last != 0;
+}
+
+__device__ __forceinline__ bool arrive_last(const Engine& e, int row) {
+    return arrive_last_n(e, row, (int)gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// real-scalar vector helpers on 16-byte units
+// ---------------------------------------------------------------------------
+template <class T> struct U16;
+template <> struct U16<float> { using t = float4; static constexpr int cpu = 2; };
+template <> struct U16<double> { using t = double2; static constexpr int cpu = 1; };
+
+__device__ __forceinline__ float4 axpy(float a, float4 x, float4 y) {
+    return {fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w)};
+}
+__device__ __forceinline__ double2 axpy(double a, double2 x, double2 y) {
+    return {fma(a, x.x, y.x), fma(a, x.y, y.y)};
+}
+// a*x + b*y
+__device__ __forceinline__ float4 axpby(float a, float4 x, float b, float4 y) {
+    return {fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z), fmaf(a, x.w, b * y.w)};
+}
+__device__ __forceinline__ double2 axpby(double a, double2 x, double b, double2 y) {
+    return {fma(a, x.x, b * y.x), fma(a, x.y, b * y.y)};
+}
+__device__ __forceinline__ float sq(float4 v) { return v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w; }
+__device__ __forceinline__ double sq(double2 v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ float4 to_unit(double2 a, double2 b) {
+    return {(float)a.x, (float)a.y, (float)b.x, (float)b.y};
 }
 
 // ---------------------------------------------------------------------------
@@ -256,6 +300,16 @@ __device__ __forceinline__ void fin_R(const Engine& e, int j, double Rn) {
         if (!finite) s->status = ST_ERR_NONFINITE;
         else if (all) s->status = ST_FINISHING;
         else if (it + 1 >= maxit) { s->status = ST_FINISHING; s->capped = 1; }
+        // reliable update (mixed precision): once the iterated residual has
+        // fallen by delta below its largest value since the last update, or
+        // after ru_every iterations, so the FP32 drift stays small relative
+        // to the residual being iterated
+        const double Rmax = fmax(s->Rmax, Rn);
+        s->Rmax = Rmax;
+        const int since = s->since_ru + 1;
+        s->since_ru = since;
+        s->ru = (s->ru_every > 0 && s->status == ST_RUNNING &&
+                 (Rn <= s->delta2 * Rmax || since >= s->ru_every)) ? 1 : 0;
     }
 }
 
@@ -279,7 +333,13 @@ __device__ __forceinline__ void fin_setR(const Engine& e, int j, double Rv, bool
         if (threadIdx.x == 0) { s->R = Rv; s->status = ST_DONE; }
         return;
     }
-    if (threadIdx.x == 0) s->R = Rv;
+    if (threadIdx.x == 0) {
+        s->R = Rv;
+        s->Rmax = Rv;
+        s->since_ru = 0;
+        s->ru = 0;
+        if (!init) s->nru += 1;
+    }
 }
 
 __device__ __forceinline__ void fin_init(const Engine& e, int j, double b2) {
@@ -288,6 +348,9 @@ __device__ __forceinline__ void fin_init(const Engine& e, int j, double b2) {
     __syncthreads();
     if (threadIdx.x == 0) {
         s->R = b2;
+        s->Rmax = b2;
+        s->since_ru = 0;
+        s->ru = 0;
         s->bnorm2 = b2;
         if (!isfinite(b2)) s->status = ST_ERR_NONFINITE;
         else if (b2 == 0.0) s->status = ST_DONE;
@@ -315,7 +378,8 @@ __device__ __forceinline__ void finalize(const Engine& e, const PassDesc& d, dou
 // Gate at kernel entry: true if this pass has nothing to do.
 __device__ __forceinline__ bool gated_off(const Engine& e, const PassDesc& d) {
     if (d.sys < 0) return false;
-    return load_status(&e.sys[d.sys]) != ST_RUNNING;
+    if (load_status(&e.sys[d.sys]) != ST_RUNNING) return true;
+    return d.gate == 1 && __ldcg(&e.sys[d.sys].ru) == 0;
 }
 
 }  // namespace msc

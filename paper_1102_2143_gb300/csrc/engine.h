@@ -67,7 +67,7 @@ cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int n
 cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st);
 cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
                              int nsys, cudaStream_t st);
-cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, cudaStream_t st);
+cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int only_ru, cudaStream_t st);
 cudaError_t launch_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n,
                            cudaStream_t st);
 
@@ -81,6 +81,46 @@ cudaError_t stag_export_bsr(const OpDev& op, int64_t* row_ptr, int32_t* col, dou
                             cudaStream_t st);
 cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
                      const double2* d_vals, int* d_bad, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// batched uneven systems (batch.cu): many staggered operators, one launch per
+// pass. Blocks are flattened over systems: block b serves system j with
+// map[j] <= b < map[j+1] (separate maps for site and vector kernels).
+// ---------------------------------------------------------------------------
+struct BOp {             // one staggered operator of a batch
+    StagGeom g;
+    int nc, recon;
+    const void* l32;
+    const double2* l64;
+};
+struct BSys {            // one system of a batch: a right-hand side (or a refined shift)
+    int64_t voff;        // offset (complex) of its r, p, t and t64 rows
+    int64_t soff;        // offset (complex) of its first shift slot in x64 / xit / ps
+    int64_t boff;        // offset (complex) of its source in b64
+    int npad;            // vector length (complex, multiple of 64)
+    int op;              // index into the operator table
+};
+struct BVec {            // base pointers of the batch's vectors
+    void* r;
+    void* p;
+    void* t;
+    void* ps;
+    void* xit;           // FP32 x accumulators (mixed) or the FP64 x (FP64)
+    double2* x64;
+    double2* t64;
+    const double2* b64;
+};
+cudaError_t launch_b_stag(int prec, int kind, int out_f32, const Engine& e, const PassDesc* descs,
+                          const BSys* sys, const BOp* ops, const int* map, int J, int nblk, int threads,
+                          cudaStream_t st);
+cudaError_t launch_b_init(int prec, const Engine& e, const BVec& v, const BSys* sys, const int* map,
+                          int J, int nblk, int threads, cudaStream_t st);
+cudaError_t launch_b_init_from_r(int prec, const Engine& e, const BVec& v, const BSys* sys,
+                                 const int* map, int J, int nblk, int threads, cudaStream_t st);
+cudaError_t launch_b_update(int prec, int units, const Engine& e, const BVec& v, const BSys* sys,
+                            const int* map, int J, int nblk, int threads, cudaStream_t st);
+cudaError_t launch_b_fold(const Engine& e, const BVec& v, const BSys* sys, const int* map, int J,
+                          int nblk, int threads, int only_ru, cudaStream_t st);
 
 // adjoint (force.cu)
 cudaError_t launch_quad(const Engine& e, const double2* phi, const double2* x, const double* c, int S,

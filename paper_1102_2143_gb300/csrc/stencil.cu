@@ -13,118 +13,9 @@
 // ([mu][component][site]) so that a warp's link loads are contiguous. In
 // FP32, SU(3) links keep two rows (third = conj(row0 x row1)) and SU(2)
 // links keep one row (second = (-conj u01, conj u00)).
-#include "engine.h"
+#include "stencil.cuh"
 
 namespace msc {
-
-template <class T> using T2 = typename C2<T>::t;
-
-struct SiteNbrs {
-    int fwd[4], bwd[4];
-    int par[4];  // parity of x_0 + ... + x_{mu-1}
-};
-
-__device__ __forceinline__ SiteNbrs neighbours(int x, const StagGeom& g) {
-    SiteNbrs nb;
-    int c[4];
-    int rem = x;
-    c[0] = rem % g.L[0]; rem /= g.L[0];
-    c[1] = rem % g.L[1]; rem /= g.L[1];
-    c[2] = rem % g.L[2]; rem /= g.L[2];
-    c[3] = rem;
-    int stride = 1, psum = 0;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        const int L = g.L[mu];
-        nb.fwd[mu] = (c[mu] == L - 1) ? x - (L - 1) * stride : x + stride;
-        nb.bwd[mu] = (c[mu] == 0) ? x + (L - 1) * stride : x - stride;
-        nb.par[mu] = psum & 1;
-        psum += c[mu];
-        stride *= L;
-    }
-    return nb;
-}
-
-// ---------------------------------------------------------------------------
-// link loads
-// ---------------------------------------------------------------------------
-template <class T, int NC, int RECON> struct Links;
-
-// full storage: T2 [4][NC*NC][V]
-template <class T, int NC> struct Links<T, NC, 0> {
-    __device__ static __forceinline__ void load(const void* base, int mu, int x, int V,
-                                                T2<T> (&u)[NC][NC]) {
-        const T2<T>* U = (const T2<T>*)base + (size_t)mu * NC * NC * V + x;
-#pragma unroll
-        for (int a = 0; a < NC; ++a)
-#pragma unroll
-            for (int b = 0; b < NC; ++b) u[a][b] = U[(size_t)(a * NC + b) * V];
-    }
-};
-
-// SU(3), two rows in three float4: (u00,u01) (u02,u10) (u11,u12)
-template <> struct Links<float, 3, 1> {
-    __device__ static __forceinline__ void load(const void* base, int mu, int x, int V,
-                                                float2 (&u)[3][3]) {
-        const float4* U = (const float4*)base + (size_t)mu * 3 * V + x;
-        const float4 q0 = U[0], q1 = U[(size_t)V], q2 = U[(size_t)2 * V];
-        u[0][0] = {q0.x, q0.y}; u[0][1] = {q0.z, q0.w};
-        u[0][2] = {q1.x, q1.y}; u[1][0] = {q1.z, q1.w};
-        u[1][1] = {q2.x, q2.y}; u[1][2] = {q2.z, q2.w};
-        // row 2 = conj(row0 x row1)
-        u[2][0] = cconj(csub(cmul(u[0][1], u[1][2]), cmul(u[0][2], u[1][1])));
-        u[2][1] = cconj(csub(cmul(u[0][2], u[1][0]), cmul(u[0][0], u[1][2])));
-        u[2][2] = cconj(csub(cmul(u[0][0], u[1][1]), cmul(u[0][1], u[1][0])));
-    }
-};
-
-// SU(2), one row in one float4: (u00,u01); row 1 = (-conj u01, conj u00)
-template <> struct Links<float, 2, 1> {
-    __device__ static __forceinline__ void load(const void* base, int mu, int x, int V,
-                                                float2 (&u)[2][2]) {
-        const float4 q = ((const float4*)base)[(size_t)mu * V + x];
-        u[0][0] = {q.x, q.y};
-        u[0][1] = {q.z, q.w};
-        u[1][0] = {-q.z, q.w};
-        u[1][1] = {q.x, -q.y};
-    }
-};
-
-// y = D src at site x
-template <class T, int NC, int RECON>
-__device__ __forceinline__ void dslash_site(const void* links, const T2<T>* __restrict__ src, int x,
-                                            const StagGeom& g, T2<T> (&y)[NC]) {
-    const SiteNbrs nb = neighbours(x, g);
-#pragma unroll
-    for (int a = 0; a < NC; ++a) y[a] = {T(0), T(0)};
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        T2<T> u[NC][NC], v[NC];
-        Links<T, NC, RECON>::load(links, mu, x, g.V, u);
-#pragma unroll
-        for (int b = 0; b < NC; ++b) v[b] = src[(size_t)nb.fwd[mu] * NC + b];
-        T2<T> w[NC][NC], z[NC];
-        Links<T, NC, RECON>::load(links, mu, nb.bwd[mu], g.V, w);
-#pragma unroll
-        for (int b = 0; b < NC; ++b) z[b] = src[(size_t)nb.bwd[mu] * NC + b];
-        const T eta = nb.par[mu] ? T(-0.5) : T(0.5);
-#pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            T2<T> f = {T(0), T(0)};
-#pragma unroll
-            for (int b = 0; b < NC; ++b) {
-                cfma(f, u[a][b], v[b]);        // + U_mu(x) src(x+mu)
-                cfms_conj(f, w[b][a], z[b]);   // - U_mu(x-mu)^dag src(x-mu)
-            }
-            y[a].x = fma(eta, f.x, y[a].x);
-            y[a].y = fma(eta, f.y, y[a].y);
-        }
-    }
-}
-
-template <class T2v> __device__ __forceinline__ double norm2d(T2v v) {
-    return (double)v.x * v.x + (double)v.y * v.y;
-}
 
 // One D pass over every site with the epilogue `KIND` (see PASS_* in engine.h).
 template <class T, int NC, int RECON, int KIND, class TO>
@@ -132,64 +23,10 @@ __global__ void __launch_bounds__(kThreads) k_stag(Engine e, const PassDesc* des
                                                    const void* links) {
     const PassDesc d = descs[blockIdx.y];
     if (gated_off(e, d)) return;
-    const T2<T>* __restrict__ src = (const T2<T>*)d.src;
-    const T2<T>* __restrict__ aux = (const T2<T>*)d.aux;
-    const T dd = (T)d.d;
-    T alpha = T(0);
-    if (KIND == PASS_B) alpha = (T)e.sys[d.sys].alpha;
+    const T alpha = KIND == PASS_B ? (T)e.sys[d.sys].alpha : T(0);
     double local = 0.0;
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.V; x += gridDim.x * blockDim.x) {
-        T2<T> y[NC];
-        dslash_site<T, NC, RECON>(links, src, x, g, y);
-        if (KIND == PASS_A) {
-            T2<T>* out = (T2<T>*)d.out;
-            T loc = T(0);
-#pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                out[(size_t)x * NC + a] = y[a];
-                if (d.row >= 0) {
-                    const T2<T> pa = aux[(size_t)x * NC + a];
-                    loc += dd * (pa.x * pa.x + pa.y * pa.y) + y[a].x * y[a].x + y[a].y * y[a].y;
-                }
-            }
-            local += (double)loc;
-        } else if (KIND == PASS_B) {
-            T2<T>* r = (T2<T>*)d.out;
-            T loc = T(0);
-#pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const T2<T> pa = aux[(size_t)x * NC + a];
-                const T2<T> ap = {dd * pa.x - y[a].x, dd * pa.y - y[a].y};
-                T2<T> ra = r[(size_t)x * NC + a];
-                ra.x -= alpha * ap.x;
-                ra.y -= alpha * ap.y;
-                r[(size_t)x * NC + a] = ra;
-                loc += ra.x * ra.x + ra.y * ra.y;
-            }
-            local += (double)loc;
-        } else if (KIND == PASS_C) {
-            TO* out = (TO*)d.out;
-#pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const T2<T> xa = aux[(size_t)x * NC + a];
-                const double2 ba = d.b[(size_t)x * NC + a];
-                const double vx = ba.x - ((double)dd * xa.x - y[a].x);
-                const double vy = ba.y - ((double)dd * xa.y - y[a].y);
-                if (out) {
-                    out[2 * ((size_t)x * NC + a)] = (TO)vx;
-                    out[2 * ((size_t)x * NC + a) + 1] = (TO)vy;
-                }
-                local += vx * vx + vy * vy;
-            }
-        } else {  // PASS_D
-            T2<T>* out = (T2<T>*)d.out;
-#pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const T2<T> xa = aux[(size_t)x * NC + a];
-                out[(size_t)x * NC + a] = {dd * xa.x - y[a].x, dd * xa.y - y[a].y};
-            }
-        }
-    }
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.V; x += gridDim.x * blockDim.x)
+        local += stag_site<T, NC, RECON, KIND, TO>(d, g, links, alpha, x);
     if (d.row >= 0) {
         double tot;
         if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);

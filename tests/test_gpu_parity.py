@@ -290,3 +290,19 @@ def test_context_reuse_across_sizes(ctx):
         assert np.all(rho <= 1e-10)
     msc.msc_op_destroy(op)
     msc.msc_op_destroy(bop)
+
+
+def test_mixed_reliable_updates_keep_fast_convergence_stable(ctx):
+    """A small SU(2) lattice whose residual falls by several decades between
+    fixed-period reliable updates: with updates triggered by the residual's
+    fall (delta 0.01) the mixed solve converges for every right-hand side."""
+    p = inputs.staggered_problem((6, 4, 4, 6), 2, 0.05, 0.6, inputs.log_shifts(1e-4, 1.0, 8), 2,
+                                 1e-10, 7010)
+    op = stag_op(ctx, p.links, p.dims, p.nc, p.mass)
+    for r in range(2):
+        x, info = msc.solve(ctx, op, p.b[r], p.sigma, precision=msc.MSC_MIXED)
+        assert info.status == 0 and info.reliable_updates > 0
+        ref = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, p.b[r], p.sigma, 1e-13)
+        rho = oracle.true_residual_staggered(p.links, p.dims, p.nc, p.mass, p.b[r], p.sigma, x)
+        check_solution(x, ref.x, rho)
+    msc.msc_op_destroy(op)
