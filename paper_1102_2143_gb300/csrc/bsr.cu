@@ -84,9 +84,11 @@ __device__ __forceinline__ void bsr_row(const OpDev& A, const T2<T>* __restrict_
     }
 }
 
+// FP32: at most 48 registers, so that five 256-thread blocks fit an SM (the
+// row loop is latency-bound and wants every resident warp).
 template <class T, int BD, int KIND, class TO>
-__global__ void __launch_bounds__(kThreads) k_bsr(Engine e, const PassDesc* descs, OpDev A,
-                                                  const T2<T>* __restrict__ vals) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1)
+k_bsr(Engine e, const PassDesc* descs, OpDev A, const T2<T>* __restrict__ vals) {
     const PassDesc d = descs[blockIdx.y];
     if (gated_off(e, d)) return;
     const T2<T>* __restrict__ src = (const T2<T>*)d.src;
@@ -141,17 +143,21 @@ __global__ void __launch_bounds__(kThreads) k_bsr(Engine e, const PassDesc* desc
 // value and column index is read once and applied to every system of the
 // group (the refinement stage and several right-hand sides). Epilogue as
 // PASS_A, with one P reduction per system.
+// `act` (optional): the passes still to run, act[0] = their count and
+// act[1..] their indices, so that groups stay full as systems finish.
 template <class T, int BD, int G>
-__global__ void __launch_bounds__(kThreads, 2) k_bsr_multi(Engine e, const PassDesc* descs, int npass,
-                                                           OpDev A, const T2<T>* __restrict__ vals) {
+__global__ void __launch_bounds__(kThreads, G >= 8 ? 2 : (G >= 4 ? 3 : (G >= 2 ? 4 : 5)))
+k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A,
+            const T2<T>* __restrict__ vals) {
     __shared__ PassDesc sd[G];
     __shared__ unsigned s_mask;
     if (threadIdx.x == 0) s_mask = 0u;
     __syncthreads();
     if (threadIdx.x < G) {
+        const int na = act ? __ldg(act) : npass;
         const int j = blockIdx.y * G + threadIdx.x;
-        if (j < npass) {
-            sd[threadIdx.x] = descs[j];
+        if (j < na) {
+            sd[threadIdx.x] = descs[act ? __ldg(act + 1 + j) : j];
             if (!gated_off(e, sd[threadIdx.x])) atomicOr(&s_mask, 1u << threadIdx.x);
         }
     }
@@ -244,25 +250,39 @@ static cudaError_t launch_bd(int kind, int out_f32, const Engine& e, const PassD
     return cudaGetLastError();
 }
 
-template <int BD>
-static void launch_multi(const Engine& e, const PassDesc* descs, int npass, const OpDev& A,
-                         cudaStream_t st) {
-    constexpr int G = 8;
+template <int BD, int G>
+static void launch_multi_g(const Engine& e, const PassDesc* descs, int npass, const int* act, int groups,
+                           const OpDev& A, cudaStream_t st) {
     auto k = k_bsr_multi<float, BD, G>;
-    dim3 grid(resident_grid((const void*)k, A.nbr), (npass + G - 1) / G);
-    k<<<grid, kThreads, 0, st>>>(e, descs, npass, A, A.vals32);
+    dim3 grid(resident_grid((const void*)k, A.nbr), groups);
+    k<<<grid, kThreads, 0, st>>>(e, descs, npass, act, A, A.vals32);
+}
+
+template <int BD>
+static void launch_multi(const Engine& e, const PassDesc* descs, int npass, const int* act, int group,
+                         int groups, const OpDev& A, cudaStream_t st) {
+    switch (group) {
+        case 1: launch_multi_g<BD, 1>(e, descs, npass, act, groups, A, st); break;
+        case 2: launch_multi_g<BD, 2>(e, descs, npass, act, groups, A, st); break;
+        case 4: launch_multi_g<BD, 4>(e, descs, npass, act, groups, A, st); break;
+        default: launch_multi_g<BD, 8>(e, descs, npass, act, groups, A, st); break;
+    }
+}
+
+cudaError_t launch_bsr_multi(const OpDev& op, const Engine& e, const PassDesc* d_descs, int npass,
+                             const int* act, int group, int groups, cudaStream_t st) {
+    switch (op.bd) {
+        case 1: launch_multi<1>(e, d_descs, npass, act, group, groups, op, st); break;
+        case 2: launch_multi<2>(e, d_descs, npass, act, group, groups, op, st); break;
+        default: launch_multi<3>(e, d_descs, npass, act, group, groups, op, st); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
                             const PassDesc* d_descs, int npass, cudaStream_t st) {
-    if (kind == PASS_A && npass > 1 && prec == PREC_F32) {
-        switch (op.bd) {
-            case 1: launch_multi<1>(e, d_descs, npass, op, st); break;
-            case 2: launch_multi<2>(e, d_descs, npass, op, st); break;
-            default: launch_multi<3>(e, d_descs, npass, op, st); break;
-        }
-        return cudaGetLastError();
-    }
+    if (kind == PASS_A && npass > 1 && prec == PREC_F32)
+        return launch_bsr_multi(op, e, d_descs, npass, nullptr, 8, (npass + 7) / 8, st);
     if (prec == PREC_F64) {
         switch (op.bd) {
             case 1: return launch_bd<double, 1>(kind, out_f32, e, d_descs, op, op.vals64, npass, st);

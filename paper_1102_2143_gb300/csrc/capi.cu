@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -36,7 +37,9 @@ enum { D_INIT = 0, D_K1, D_K2, D_RUA, D_RUC, D_RIA, D_RIC, D_AP1, D_AP2, D_NSECT
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int gen = -1;
-    int kernels = 0;
+    int kernels = 0;       // kernels launched unconditionally per launch
+    int cond_chunk = 0;    // iterations with a conditional update body (0: none)
+    int cond_kernels = 0;  // kernels in one such body
 };
 
 long g_op_uid = 0;
@@ -55,6 +58,12 @@ struct msc_ctx {
     Buf b64, x64, t64, r, p, t, ps, xit;
     Buf coef, force;  // adjoint: weights c_s and a link-shaped output
     Buf btab;         // batched solves: system table, operator table, block maps
+    Buf actb;         // {count, indices} of the systems still iterating (refinement)
+    Buf condf;        // one flag per iteration of a chunk graph (conditional update bodies)
+    int use_cond = 1; // build reliable updates as conditional graph nodes
+    int* h_flags = nullptr;  // pinned copy of the conditional flags of a chunk
+    int* h_act = nullptr;
+    int64_t h_act_cap = 0;
     int64_t rows_cap = 0;  // rows the desc sections were laid out for
     int gen = 0;
     // pinned host mirrors
@@ -158,7 +167,7 @@ static cudaError_t upload_sec(msc_ctx* c, int s, int count) {
 }
 
 static Engine engine_of(msc_ctx* c) {
-    Engine e;
+    Engine e{};
     e.sys = (SysScalars*)c->sys.p;
     e.slot = (SlotScalars*)c->slot.p;
     e.partial = (double*)c->partial.p;
@@ -202,8 +211,8 @@ static PassDesc ru_pass(PassDesc d) {
 }
 
 static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int out_f32, int sec,
-                           int npass) {
-    Engine e = engine_of(c);
+                           int npass, const Engine* eng = nullptr) {
+    Engine e = eng ? *eng : engine_of(c);
     c->launches++;
     if (A.kind == OP_STAGGERED)
         return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work);
@@ -215,14 +224,21 @@ static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int o
 // iteration ends with the reliable-update kernels, which only do work for the
 // systems whose update is due (flag set by the iteration's finalize).
 static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys, int chunk,
-                                 bool reliable, bool profile, int64_t npad, int& kernels) {
+                                 bool reliable, bool profile, int64_t npad, int group, int groups,
+                                 int& kernels) {
     Engine e = engine_of(c);
     VecSet v = vecs_of(c, prec, npad);
     kernels = 0;
     for (int it = 0; it < chunk; ++it) {
         const bool prof = profile && it == 0;
         if (prof) cudaEventRecordWithFlags(c->prof[0], c->work, cudaEventRecordExternal);
-        cudaError_t err = op_pass(c, A, prec, PASS_A, 0, D_K1, nsys);
+        cudaError_t err;
+        if (group > 0) {
+            c->launches++;
+            err = launch_bsr_multi(A, e, dsec(c, D_K1), nsys, (const int*)c->actb.p, group, groups, c->work);
+        } else {
+            err = op_pass(c, A, prec, PASS_A, 0, D_K1, nsys);
+        }
         if (err != cudaSuccess) return err;
         if (prof) cudaEventRecordWithFlags(c->prof[1], c->work, cudaEventRecordExternal);
         if (A.kind == OP_STAGGERED) err = op_pass(c, A, prec, PASS_B, 0, D_K2, nsys);
@@ -250,11 +266,109 @@ static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys,
     return cudaSuccess;
 }
 
+static cudaError_t begin_capture_into(cudaStream_t st, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps) {
+    return cudaStreamBeginCaptureToGraph(st, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                         cudaStreamCaptureModeThreadLocal);
+}
+
+// The nodes the next captured operation would depend on (copied).
+static cudaError_t capture_tail(cudaStream_t st, std::vector<cudaGraphNode_t>& tail) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    tail.assign(deps, deps + nd);
+    return cudaSuccess;
+}
+
+// A chunk graph whose reliable-update kernels sit in one conditional IF node
+// per iteration: the iteration's residual kernel sets the condition on the
+// device when some system's update is due, so iterations without an update
+// launch nothing for it.
+static cudaError_t build_chunk_graph_cond(msc_ctx* c, const OpDev& A, int prec, int nsys, int chunk,
+                                          bool profile, int64_t npad, int group, int groups,
+                                          cudaGraph_t* out, int& kernels) {
+    bool moved = false;
+    cudaError_t err = grow(c->condf, sizeof(int) * chunk, moved);
+    if (err != cudaSuccess) return err;
+    if (moved) c->gen++;
+    int* flags = (int*)c->condf.p;
+    cudaGraph_t g = nullptr;
+    err = cudaGraphCreate(&g, 0);
+    if (err != cudaSuccess) return err;
+    VecSet v = vecs_of(c, prec, npad);
+    std::vector<cudaGraphNode_t> tail;
+    kernels = 0;
+    for (int it = 0; it < chunk && err == cudaSuccess; ++it) {
+        cudaGraphConditionalHandle h = 0;
+        err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+        if (err != cudaSuccess) break;
+        Engine e = engine_of(c);
+        Engine e2 = e;
+        e2.cond = (unsigned long long)h;
+        e2.cond_flag = flags + it;
+        err = begin_capture_into(c->work, g, tail);
+        if (err != cudaSuccess) break;
+        const bool prof = profile && it == 0;
+        if (it == 0) err = cudaMemsetAsync(flags, 0, sizeof(int) * chunk, c->work);
+        if (prof) cudaEventRecordWithFlags(c->prof[0], c->work, cudaEventRecordExternal);
+        if (err == cudaSuccess) {
+            if (group > 0) err = launch_bsr_multi(A, e, dsec(c, D_K1), nsys, (const int*)c->actb.p, group, groups, c->work);
+            else err = op_pass(c, A, prec, PASS_A, 0, D_K1, nsys, &e);
+        }
+        if (prof) cudaEventRecordWithFlags(c->prof[1], c->work, cudaEventRecordExternal);
+        if (err == cudaSuccess) {
+            if (A.kind == OP_STAGGERED) err = op_pass(c, A, prec, PASS_B, 0, D_K2, nsys, &e2);
+            else err = launch_axpy_norm(prec, e2, v, dsec(c, D_K2), nsys, c->work);
+        }
+        if (prof) cudaEventRecordWithFlags(c->prof[2], c->work, cudaEventRecordExternal);
+        if (err == cudaSuccess) err = launch_update(prec, e, v, nsys, c->work);
+        if (prof) cudaEventRecordWithFlags(c->prof[3], c->work, cudaEventRecordExternal);
+        kernels += 3;
+        cudaError_t et = capture_tail(c->work, tail);
+        cudaGraph_t gg = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(c->work, &gg);
+        if (err == cudaSuccess) err = et != cudaSuccess ? et : ee;
+        if (err != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t ifn = nullptr;
+        err = cudaGraphAddNode(&ifn, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(), &cp);
+        if (err != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        err = begin_capture_into(c->work, body, {});
+        if (err != cudaSuccess) break;
+        err = launch_fold(e, v, nsys, 1, c->work);
+        if (err == cudaSuccess && A.kind == OP_STAGGERED) err = op_pass(c, A, PREC_F64, PASS_A, 0, D_RUA, nsys, &e);
+        if (err == cudaSuccess) err = op_pass(c, A, PREC_F64, PASS_C, 1, D_RUC, nsys, &e);
+        ee = cudaStreamEndCapture(c->work, &gg);
+        if (err == cudaSuccess) err = ee;
+        tail.assign(1, ifn);
+    }
+    if (err != cudaSuccess) {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(c->work, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(c->work, &junk);
+            if (junk && junk != g) cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return err;
+    }
+    *out = g;
+    return cudaSuccess;
+}
+
 static int get_graph(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk, bool reliable,
-                     bool profile, int64_t npad, GraphEntry** out) {
+                     bool profile, int64_t npad, int group, int groups, GraphEntry** out) {
     char key[160];
-    snprintf(key, sizeof key, "%ld|%d|%d|%d|%d|%d|%lld", op->uid, prec, nsys, chunk, (int)reliable,
-             (int)profile, (long long)npad);
+    snprintf(key, sizeof key, "%ld|%d|%d|%d|%d|%d|%lld|%d|%d", op->uid, prec, nsys, chunk, (int)reliable,
+             (int)profile, (long long)npad, group, groups);
     GraphEntry& ge = c->graphs[key];
     if (ge.exec && ge.gen == c->gen) {
         *out = &ge;
@@ -265,19 +379,33 @@ static int get_graph(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
         ge.exec = nullptr;
     }
     long saved = c->launches;
-    CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
     int kernels = 0;
-    cudaError_t err = enqueue_chunk(c, op->dev, prec, nsys, chunk, reliable, profile, npad, kernels);
     cudaGraph_t g = nullptr;
-    cudaError_t err2 = cudaStreamEndCapture(c->work, &g);
+    cudaError_t err = cudaErrorNotSupported;
+    if (reliable && c->use_cond) {
+        err = build_chunk_graph_cond(c, op->dev, prec, nsys, chunk, profile, npad, group, groups, &g, kernels);
+        if (err != cudaSuccess) {
+            c->use_cond = 0;  // conditional nodes unavailable: gate the update kernels instead
+            cudaGetLastError();
+        }
+    }
+    if (err != cudaSuccess) {
+        CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
+        err = enqueue_chunk(c, op->dev, prec, nsys, chunk, reliable, profile, npad, group, groups, kernels);
+        cudaError_t err2 = cudaStreamEndCapture(c->work, &g);
+        if (err != cudaSuccess) { if (g) cudaGraphDestroy(g); c->launches = saved; return cuda_status(err); }
+        if (err2 != cudaSuccess) { c->launches = saved; return cuda_status(err2); }
+    }
     c->launches = saved;
-    if (err != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_status(err); }
-    if (err2 != cudaSuccess) return cuda_status(err2);
+    const bool cond = reliable && c->use_cond;
     err = cudaGraphInstantiate(&ge.exec, g, 0);
     cudaGraphDestroy(g);
     if (err != cudaSuccess) return cuda_status(err);
     ge.gen = c->gen;
     ge.kernels = kernels;
+    ge.cond_chunk = cond ? chunk : 0;
+    ge.cond_kernels = op->dev.kind == OP_STAGGERED ? 3 : 2;
+    if (cond && !c->h_flags) CK(cudaMallocHost((void**)&c->h_flags, sizeof(int) * 1024));
     *out = &ge;
     return MSC_OK;
 }
@@ -287,27 +415,58 @@ struct ProfAcc {
     int n = 0;
 };
 
-// Launch chunks until every system has stopped.
+// Launch chunks until every system has stopped. With `compact` (several
+// systems sharing a block-CSR matrix in FP32), the SpMV of each chunk runs
+// only the systems still iterating, in groups sized for their number.
 static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk, bool reliable,
-                     bool profile, int64_t npad, int max_iter, ProfAcc* pa, int* rel_updates) {
+                     bool profile, int64_t npad, int max_iter, ProfAcc* pa, int* rel_updates,
+                     bool compact = false) {
+    compact = compact && op->dev.kind == OP_BSR && prec == PREC_F32 && nsys > 1;
+    if (compact) {
+        bool moved = false;
+        CK(grow(c->actb, sizeof(int) * (nsys + 1), moved));
+        if (moved) c->gen++;
+        if (c->h_act_cap < nsys + 1) {
+            if (c->h_act) cudaFreeHost(c->h_act);
+            CK(cudaMallocHost((void**)&c->h_act, sizeof(int) * (nsys + 1)));
+            c->h_act_cap = nsys + 1;
+        }
+    }
     GraphEntry* ge = nullptr;
-    int st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, &ge);
-    if (st != MSC_OK) return st;
+    int st = MSC_OK;
+    if (!compact) {
+        st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, 0, 0, &ge);
+        if (st != MSC_OK) return st;
+    }
     CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost, c->work));
     CK(cudaStreamSynchronize(c->work));
     const long max_chunks = (long)max_iter / chunk + 2;
     for (long k = 0; k < max_chunks; ++k) {
         bool any = false, all_running = true;
+        int active = 0;
         for (int j = 0; j < nsys; ++j) {
             if (c->h_sys[j].status < ST_DONE) any = true;
             if (c->h_sys[j].status != ST_RUNNING) all_running = false;
+            else if (compact) c->h_act[1 + active++] = j;
         }
         if (!any) break;
+        if (compact) {
+            const int group = active <= 1 ? 1 : (active <= 2 ? 2 : (active <= 4 ? 4 : 8));
+            const int groups = (active + group - 1) / group;
+            c->h_act[0] = active;
+            CK(cudaMemcpyAsync(c->actb.p, c->h_act, sizeof(int) * (active + 1), cudaMemcpyHostToDevice,
+                               c->work));
+            st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, group, groups, &ge);
+            if (st != MSC_OK) return st;
+        }
         CK(cudaGraphLaunch(ge->exec, c->work));
         c->launches += ge->kernels;
         CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost,
                            c->work));
+        const int ncf = std::min(ge->cond_chunk, 1024);
+        if (ncf) CK(cudaMemcpyAsync(c->h_flags, c->condf.p, sizeof(int) * ncf, cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
+        for (int i = 0; i < ncf; ++i) c->launches += c->h_flags[i] ? ge->cond_kernels : 0;
         if (profile && pa && all_running) {
             float a = 0, b = 0, d = 0;
             if (cudaEventElapsedTime(&a, c->prof[0], c->prof[1]) == cudaSuccess &&
@@ -396,6 +555,10 @@ int msc_create(msc_ctx** out, int device, void* stream) {
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     c->user = (cudaStream_t)stream;
+    // MSC_GRAPH_COND=0 builds reliable updates as always-launched kernels that
+    // exit when no update is due, instead of conditional graph nodes (for
+    // profilers that replay kernels one by one)
+    if (const char* ev = getenv("MSC_GRAPH_COND")) c->use_cond = atoi(ev) != 0;
     cudaError_t e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sync, cudaEventDisableTiming);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->prof[i]);
@@ -421,13 +584,15 @@ int msc_destroy(msc_ctx* c) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     Buf* bufs[] = {&c->sys, &c->slot, &c->partial, &c->counter, &c->out_red, &c->descs,
                    &c->b64, &c->x64, &c->t64, &c->r, &c->p, &c->t, &c->ps, &c->xit,
-                   &c->coef, &c->force, &c->btab};
+                   &c->coef, &c->force, &c->btab, &c->actb, &c->condf};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_sys) cudaFreeHost(c->h_sys);
     if (c->h_slot) cudaFreeHost(c->h_slot);
     if (c->h_red) cudaFreeHost(c->h_red);
     if (c->h_desc) cudaFreeHost(c->h_desc);
+    if (c->h_act) cudaFreeHost(c->h_act);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
     if (c->ev_sync) cudaEventDestroy(c->ev_sync);
     for (int i = 0; i < 4; ++i)
         if (c->prof[i]) cudaEventDestroy(c->prof[i]);
@@ -884,7 +1049,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
             if (check_only || next.empty() || status != MSC_OK) break;
             CK(launch_init_from_r(prec, e, v, m, c->work));
             c->launches++;
-            st = run_stage(c, op, prec, m, chunk, mixed, false, npad, prm.max_iter, nullptr, &rel_ref);
+            st = run_stage(c, op, prec, m, chunk, mixed, false, npad, prm.max_iter, nullptr, &rel_ref, true);
             if (st) return st;
             int most = 0;
             for (int k = 0; k < m; ++k) {

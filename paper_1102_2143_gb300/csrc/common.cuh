@@ -99,6 +99,10 @@ struct Engine {
     double* partial;     // [rows][kMaxBlocks]
     unsigned* counter;   // [rows]
     double* out_red;     // [rows]
+    // CUDA-graph conditional of this iteration's reliable-update body (0: none)
+    // and the flag that lets exactly one system set it
+    unsigned long long cond;
+    int* cond_flag;
 };
 
 // ---------------------------------------------------------------------------
@@ -308,8 +312,11 @@ __device__ __forceinline__ void fin_R(const Engine& e, int j, double Rn) {
         s->Rmax = Rmax;
         const int since = s->since_ru + 1;
         s->since_ru = since;
-        s->ru = (s->ru_every > 0 && s->status == ST_RUNNING &&
-                 (Rn <= s->delta2 * Rmax || since >= s->ru_every)) ? 1 : 0;
+        const int ru = (s->ru_every > 0 && s->status == ST_RUNNING &&
+                        (Rn <= s->delta2 * Rmax || since >= s->ru_every)) ? 1 : 0;
+        s->ru = ru;
+        if (ru && e.cond_flag && atomicExch(e.cond_flag, 1) == 0)
+            cudaGraphSetConditional((cudaGraphConditionalHandle)e.cond, 1u);
     }
 }
 

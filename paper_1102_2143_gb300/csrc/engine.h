@@ -48,6 +48,11 @@ cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, c
                              const PassDesc* d_descs, int npass, cudaStream_t st);
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
                             const PassDesc* d_descs, int npass, cudaStream_t st);
+// FP32 SpMV of several systems sharing the matrix, `group` (1, 2, 4, 8)
+// systems per block row of the grid, `groups` rows; `act` (device, optional)
+// = {count, indices...} of the systems to run, read when the kernel runs.
+cudaError_t launch_bsr_multi(const OpDev& op, const Engine& e, const PassDesc* d_descs, int npass,
+                             const int* act, int group, int groups, cudaStream_t st);
 
 // vector kernels; vectors are addressed as [index][npad] complex in the
 // iteration precision (prec) unless noted
