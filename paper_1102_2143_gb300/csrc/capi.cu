@@ -1114,68 +1114,100 @@ struct BatchShape {
 std::mutex g_tune_mu;
 std::map<std::string, std::pair<BatchShape, double>> g_tune_cache;
 
-// Device-side tables of one stage of a batched solve.
-struct BatchDev {
-    BSys* sys = nullptr;
-    BOp* ops = nullptr;
-    int* msite = nullptr;  // blocks of the operator passes
-    int* mvec = nullptr;   // one unit per thread (init, fold)
-    int* mupd = nullptr;   // `units` units per thread (update)
-    int nsite = 0, nvec = 0, nupd = 0;
-};
-
 }  // namespace
 
 static int64_t pad64(int64_t n) { return (n + 63) / 64 * 64; }
+static size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
-// Prefix-sum block maps of the systems for one launch shape; uploads the
-// system and operator tables with them (into c->btab).
-static int upload_batch_tables(msc_ctx* c, const std::vector<BSys>& sys, const std::vector<BOp>& ops,
-                               const BatchShape& sh, int prec, BatchDev& bd) {
-    const int J = (int)sys.size();
+// Device tables of a batched stage live in c->btab:
+//   [BSys x cap][BOp x nops][hdr 4][act cap][msite cap+1][mvec cap+1][mupd cap+1]
+// The last five are rewritten (from pinned staging) whenever the set of
+// systems still iterating changes; kernels read them when they run.
+struct BatchHost {
+    int cap = 0, nops = 0;
+    size_t off_ops = 0, off_hdr = 0, off_act = 0, off_ms = 0, off_mv = 0, off_mu = 0, total = 0;
+    BTab tab{};
+};
+
+static int batch_layout(msc_ctx* c, int cap, int nops, BatchHost& bh) {
+    bh.cap = cap;
+    bh.nops = nops;
+    bh.off_ops = al256(sizeof(BSys) * cap);
+    bh.off_hdr = bh.off_ops + al256(sizeof(BOp) * nops);
+    bh.off_act = bh.off_hdr + 256;
+    bh.off_ms = bh.off_act + al256(sizeof(int) * cap);
+    bh.off_mv = bh.off_ms + al256(sizeof(int) * (cap + 1));
+    bh.off_mu = bh.off_mv + al256(sizeof(int) * (cap + 1));
+    bh.total = bh.off_mu + al256(sizeof(int) * (cap + 1));
+    bool moved = false;
+    CK(grow(c->btab, bh.total, moved));
+    if (moved) c->gen++;
+    if (c->h_act_cap < (int64_t)(bh.total / sizeof(int)) + 1) {
+        if (c->h_act) cudaFreeHost(c->h_act);
+        CK(cudaMallocHost((void**)&c->h_act, bh.total + 64));
+        c->h_act_cap = (int64_t)(bh.total / sizeof(int)) + 1;
+    }
+    char* base = (char*)c->btab.p;
+    bh.tab.sys = (const BSys*)base;
+    bh.tab.ops = (const BOp*)(base + bh.off_ops);
+    bh.tab.hdr = (const int*)(base + bh.off_hdr);
+    bh.tab.act = (const int*)(base + bh.off_act);
+    bh.tab.msite = (const int*)(base + bh.off_ms);
+    bh.tab.mvec = (const int*)(base + bh.off_mv);
+    bh.tab.mupd = (const int*)(base + bh.off_mu);
+    return MSC_OK;
+}
+
+static int upload_systems(msc_ctx* c, const BatchHost& bh, const std::vector<BSys>& sys,
+                          const std::vector<BOp>& ops) {
+    char* base = (char*)c->btab.p;
+    // ordered on the work stream after everything that may still read the
+    // tables; the host vectors are pageable, so wait for the copies
+    CK(cudaMemcpyAsync(base, sys.data(), sizeof(BSys) * sys.size(), cudaMemcpyHostToDevice, c->work));
+    CK(cudaMemcpyAsync(base + bh.off_ops, ops.data(), sizeof(BOp) * ops.size(), cudaMemcpyHostToDevice, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    return MSC_OK;
+}
+
+// Block maps of the systems `list` for launch shape `sh`, staged in pinned
+// memory and copied on the work stream (the caller syncs before restaging).
+static int set_active(msc_ctx* c, const BatchHost& bh, const std::vector<BSys>& sys,
+                      const std::vector<BOp>& ops, const std::vector<int>& list, const BatchShape& sh,
+                      int prec) {
+    const int J = (int)list.size();
     const int cpu = prec == PREC_F32 ? 2 : 1;
-    std::vector<int> ms(J + 1), mv(J + 1), mu(J + 1);
+    char* stage = (char*)c->h_act;
+    int* hdr = (int*)(stage + bh.off_hdr - bh.off_hdr);
+    int* act = (int*)(stage + bh.off_act - bh.off_hdr);
+    int* ms = (int*)(stage + bh.off_ms - bh.off_hdr);
+    int* mv = (int*)(stage + bh.off_mv - bh.off_hdr);
+    int* mu = (int*)(stage + bh.off_mu - bh.off_hdr);
     int64_t a = 0, b = 0, u = 0;
-    for (int j = 0; j < J; ++j) {
-        ms[j] = (int)a;
-        mv[j] = (int)b;
-        mu[j] = (int)u;
-        const int V = ops[sys[j].op].g.V;
-        const int64_t upv = sys[j].npad / cpu;
-        a += (V + sh.site_threads - 1) / sh.site_threads;
-        b += (upv + sh.vec_threads - 1) / sh.vec_threads;
+    for (int k = 0; k < J; ++k) {
+        const BSys& q = sys[list[k]];
+        act[k] = list[k];
+        ms[k] = (int)a;
+        mv[k] = (int)b;
+        mu[k] = (int)u;
+        const int V = ops[q.op].g.V;
+        const int64_t upv = q.npad / cpu;
+        const int64_t nbs = (V + sh.site_threads - 1) / sh.site_threads;
+        const int64_t nbv = (upv + sh.vec_threads - 1) / sh.vec_threads;
+        if (nbs > kMaxBlocks || nbv > kMaxBlocks) return MSC_ERR_UNSUPPORTED;
+        a += nbs;
+        b += nbv;
         u += (upv + (int64_t)sh.vec_threads * sh.units - 1) / ((int64_t)sh.vec_threads * sh.units);
         if (a >= ((int64_t)1 << 30) || b >= ((int64_t)1 << 30)) return MSC_ERR_UNSUPPORTED;
-        if ((a - ms[j]) > kMaxBlocks || (b - mv[j]) > kMaxBlocks) return MSC_ERR_UNSUPPORTED;
     }
     ms[J] = (int)a;
     mv[J] = (int)b;
     mu[J] = (int)u;
-    const size_t bsys = sizeof(BSys) * J, bops = sizeof(BOp) * ops.size(), bmap = sizeof(int) * (J + 1);
-    const size_t off_ops = (bsys + 255) / 256 * 256;
-    const size_t off_ms = off_ops + (bops + 255) / 256 * 256;
-    const size_t off_mv = off_ms + (bmap + 255) / 256 * 256;
-    const size_t off_mu = off_mv + (bmap + 255) / 256 * 256;
-    const size_t total = off_mu + bmap;
-    bool moved = false;
-    CK(grow(c->btab, total, moved));
-    if (moved) c->gen++;
-    char* base = (char*)c->btab.p;
-    CK(cudaMemcpyAsync(base, sys.data(), bsys, cudaMemcpyHostToDevice, c->work));
-    CK(cudaMemcpyAsync(base + off_ops, ops.data(), bops, cudaMemcpyHostToDevice, c->work));
-    CK(cudaMemcpyAsync(base + off_ms, ms.data(), bmap, cudaMemcpyHostToDevice, c->work));
-    CK(cudaMemcpyAsync(base + off_mv, mv.data(), bmap, cudaMemcpyHostToDevice, c->work));
-    CK(cudaMemcpyAsync(base + off_mu, mu.data(), bmap, cudaMemcpyHostToDevice, c->work));
-    // the host vectors above are pageable: wait before they go out of scope
-    CK(cudaStreamSynchronize(c->work));
-    bd.sys = (BSys*)base;
-    bd.ops = (BOp*)(base + off_ops);
-    bd.msite = (int*)(base + off_ms);
-    bd.mvec = (int*)(base + off_mv);
-    bd.mupd = (int*)(base + off_mu);
-    bd.nsite = (int)a;
-    bd.nvec = (int)b;
-    bd.nupd = (int)u;
+    hdr[0] = J;
+    hdr[1] = (int)a;
+    hdr[2] = (int)b;
+    hdr[3] = (int)u;
+    CK(cudaMemcpyAsync((char*)c->btab.p + bh.off_hdr, stage, bh.total - bh.off_hdr, cudaMemcpyHostToDevice,
+                       c->work));
     return MSC_OK;
 }
 
@@ -1192,69 +1224,165 @@ static BVec bvec_of(msc_ctx* c, int prec) {
     return v;
 }
 
-static cudaError_t enqueue_chunk_b(msc_ctx* c, int prec, int J, int chunk, bool reliable,
-                                   const BatchDev& bd, const BatchShape& sh, int& kernels) {
+// One chunk of the batched iteration (plain capture; reliable updates as
+// gated kernels).
+static cudaError_t enqueue_chunk_b(msc_ctx* c, int prec, int chunk, bool reliable, const BTab& t,
+                                   const BatchShape& sh, int& kernels) {
     Engine e = engine_of(c);
     BVec v = bvec_of(c, prec);
     kernels = 0;
     cudaError_t err = cudaSuccess;
     for (int it = 0; it < chunk && err == cudaSuccess; ++it) {
-        err = launch_b_stag(prec, PASS_A, 0, e, dsec(c, D_K1), bd.sys, bd.ops, bd.msite, J, bd.nsite,
-                            sh.site_threads, c->work);
-        if (err == cudaSuccess)
-            err = launch_b_stag(prec, PASS_B, 0, e, dsec(c, D_K2), bd.sys, bd.ops, bd.msite, J, bd.nsite,
-                                sh.site_threads, c->work);
-        if (err == cudaSuccess)
-            err = launch_b_update(prec, sh.units, e, v, bd.sys, bd.mupd, J, bd.nupd, sh.vec_threads, c->work);
+        err = launch_b_stag(prec, PASS_A, 0, e, dsec(c, D_K1), t, sh.site_threads, c->work);
+        if (err == cudaSuccess) err = launch_b_stag(prec, PASS_B, 0, e, dsec(c, D_K2), t, sh.site_threads, c->work);
+        if (err == cudaSuccess) err = launch_b_update(prec, sh.units, e, v, t, sh.vec_threads, c->work);
         kernels += 3;
         if (reliable && err == cudaSuccess) {
-            err = launch_b_fold(e, v, bd.sys, bd.mvec, J, bd.nvec, sh.vec_threads, 1, c->work);
-            if (err == cudaSuccess)
-                err = launch_b_stag(PREC_F64, PASS_A, 0, e, dsec(c, D_RUA), bd.sys, bd.ops, bd.msite, J,
-                                    bd.nsite, sh.site_threads, c->work);
-            if (err == cudaSuccess)
-                err = launch_b_stag(PREC_F64, PASS_C, 1, e, dsec(c, D_RUC), bd.sys, bd.ops, bd.msite, J,
-                                    bd.nsite, sh.site_threads, c->work);
+            err = launch_b_fold(e, v, t, sh.vec_threads, 1, c->work);
+            if (err == cudaSuccess) err = launch_b_stag(PREC_F64, PASS_A, 0, e, dsec(c, D_RUA), t, sh.site_threads, c->work);
+            if (err == cudaSuccess) err = launch_b_stag(PREC_F64, PASS_C, 1, e, dsec(c, D_RUC), t, sh.site_threads, c->work);
             kernels += 3;
         }
     }
     return err;
 }
 
-static int run_stage_b(msc_ctx* c, int prec, int J, int chunk, bool reliable, const BatchDev& bd,
-                       const BatchShape& sh, int max_iter, int* rel_updates) {
+// The same chunk with each iteration's reliable-update kernels in a
+// conditional IF node set on the device by the residual pass.
+static cudaError_t build_chunk_graph_b_cond(msc_ctx* c, int prec, int chunk, const BTab& t,
+                                            const BatchShape& sh, cudaGraph_t* out, int& kernels) {
+    bool moved = false;
+    cudaError_t err = grow(c->condf, sizeof(int) * chunk, moved);
+    if (err != cudaSuccess) return err;
+    if (moved) c->gen++;
+    int* flags = (int*)c->condf.p;
+    cudaGraph_t g = nullptr;
+    err = cudaGraphCreate(&g, 0);
+    if (err != cudaSuccess) return err;
+    BVec v = bvec_of(c, prec);
+    std::vector<cudaGraphNode_t> tail;
+    kernels = 0;
+    for (int it = 0; it < chunk && err == cudaSuccess; ++it) {
+        cudaGraphConditionalHandle h = 0;
+        err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+        if (err != cudaSuccess) break;
+        Engine e = engine_of(c);
+        Engine e2 = e;
+        e2.cond = (unsigned long long)h;
+        e2.cond_flag = flags + it;
+        err = begin_capture_into(c->work, g, tail);
+        if (err != cudaSuccess) break;
+        if (it == 0) err = cudaMemsetAsync(flags, 0, sizeof(int) * chunk, c->work);
+        if (err == cudaSuccess) err = launch_b_stag(prec, PASS_A, 0, e, dsec(c, D_K1), t, sh.site_threads, c->work);
+        if (err == cudaSuccess) err = launch_b_stag(prec, PASS_B, 0, e2, dsec(c, D_K2), t, sh.site_threads, c->work);
+        if (err == cudaSuccess) err = launch_b_update(prec, sh.units, e, v, t, sh.vec_threads, c->work);
+        kernels += 3;
+        cudaError_t et = capture_tail(c->work, tail);
+        cudaGraph_t gg = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(c->work, &gg);
+        if (err == cudaSuccess) err = et != cudaSuccess ? et : ee;
+        if (err != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t ifn = nullptr;
+        err = cudaGraphAddNode(&ifn, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(), &cp);
+        if (err != cudaSuccess) break;
+        err = begin_capture_into(c->work, cp.conditional.phGraph_out[0], {});
+        if (err != cudaSuccess) break;
+        err = launch_b_fold(e, v, t, sh.vec_threads, 1, c->work);
+        if (err == cudaSuccess) err = launch_b_stag(PREC_F64, PASS_A, 0, e, dsec(c, D_RUA), t, sh.site_threads, c->work);
+        if (err == cudaSuccess) err = launch_b_stag(PREC_F64, PASS_C, 1, e, dsec(c, D_RUC), t, sh.site_threads, c->work);
+        ee = cudaStreamEndCapture(c->work, &gg);
+        if (err == cudaSuccess) err = ee;
+        tail.assign(1, ifn);
+    }
+    if (err != cudaSuccess) {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(c->work, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(c->work, &junk);
+            if (junk && junk != g) cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return err;
+    }
+    *out = g;
+    return cudaSuccess;
+}
+
+static int get_graph_b(msc_ctx* c, int prec, int chunk, bool reliable, const BTab& t, const BatchShape& sh,
+                       GraphEntry** out) {
     char key[200];
-    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d", prec, J, chunk, (int)reliable, bd.nsite,
-             bd.nvec, bd.nupd, sh.site_threads, sh.vec_threads, sh.units, c->gen);
+    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%p", prec, chunk, (int)reliable, sh.site_threads,
+             sh.vec_threads, sh.units, (const void*)t.sys);
     GraphEntry& ge = c->graphs[key];
-    if (!ge.exec || ge.gen != c->gen) {
-        if (ge.exec) cudaGraphExecDestroy(ge.exec);
-        ge.exec = nullptr;
+    if (ge.exec && ge.gen == c->gen) {
+        *out = &ge;
+        return MSC_OK;
+    }
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    ge.exec = nullptr;
+    int kernels = 0;
+    cudaGraph_t g = nullptr;
+    cudaError_t err = cudaErrorNotSupported;
+    if (reliable && c->use_cond) {
+        err = build_chunk_graph_b_cond(c, prec, chunk, t, sh, &g, kernels);
+        if (err != cudaSuccess) {
+            c->use_cond = 0;
+            cudaGetLastError();
+        }
+    }
+    if (err != cudaSuccess) {
         CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
-        int kernels = 0;
-        cudaError_t err = enqueue_chunk_b(c, prec, J, chunk, reliable, bd, sh, kernels);
-        cudaGraph_t g = nullptr;
+        err = enqueue_chunk_b(c, prec, chunk, reliable, t, sh, kernels);
         cudaError_t err2 = cudaStreamEndCapture(c->work, &g);
         if (err != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_status(err); }
         if (err2 != cudaSuccess) return cuda_status(err2);
-        err = cudaGraphInstantiate(&ge.exec, g, 0);
-        cudaGraphDestroy(g);
-        if (err != cudaSuccess) return cuda_status(err);
-        ge.gen = c->gen;
-        ge.kernels = kernels;
     }
+    const bool cond = reliable && c->use_cond;
+    err = cudaGraphInstantiate(&ge.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return cuda_status(err);
+    ge.gen = c->gen;
+    ge.kernels = kernels;
+    ge.cond_chunk = cond ? chunk : 0;
+    ge.cond_kernels = 3;
+    if (cond && !c->h_flags) CK(cudaMallocHost((void**)&c->h_flags, sizeof(int) * 1024));
+    *out = &ge;
+    return MSC_OK;
+}
+
+// Launch chunks until every system of the stage has stopped; before each
+// chunk the active maps are rebuilt from the systems still iterating.
+static int run_stage_b(msc_ctx* c, int prec, int J, int chunk, bool reliable, const BatchHost& bh,
+                       const std::vector<BSys>& sys, const std::vector<BOp>& ops, const BatchShape& sh,
+                       int max_iter, int* rel_updates) {
+    GraphEntry* ge = nullptr;
+    int st = get_graph_b(c, prec, chunk, reliable, bh.tab, sh, &ge);
+    if (st) return st;
     CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * J, cudaMemcpyDeviceToHost, c->work));
     CK(cudaStreamSynchronize(c->work));
     const long max_chunks = (long)max_iter / chunk + 2;
+    std::vector<int> list;
+    list.reserve(J);
     for (long k = 0; k < max_chunks; ++k) {
-        bool any = false;
+        list.clear();
         for (int j = 0; j < J; ++j)
-            if (c->h_sys[j].status < ST_DONE) any = true;
-        if (!any) break;
-        CK(cudaGraphLaunch(ge.exec, c->work));
-        c->launches += ge.kernels;
+            if (c->h_sys[j].status == ST_RUNNING) list.push_back(j);
+        if (list.empty()) break;
+        st = set_active(c, bh, sys, ops, list, sh, prec);
+        if (st) return st;
+        CK(cudaGraphLaunch(ge->exec, c->work));
+        c->launches += ge->kernels;
         CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * J, cudaMemcpyDeviceToHost, c->work));
+        const int ncf = std::min(ge->cond_chunk, 1024);
+        if (ncf) CK(cudaMemcpyAsync(c->h_flags, c->condf.p, sizeof(int) * ncf, cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
+        for (int i = 0; i < ncf; ++i) c->launches += c->h_flags[i] ? ge->cond_kernels : 0;
     }
     if (rel_updates)
         for (int j = 0; j < J; ++j) *rel_updates += c->h_sys[j].nru;
@@ -1264,8 +1392,8 @@ static int run_stage_b(msc_ctx* c, int prec, int J, int chunk, bool reliable, co
 // Times candidate launch shapes on the batch (operator pass + update, with
 // reductions that finalise nothing) and returns the fastest. Runs before the
 // solve initialises its vectors, on whatever they hold.
-static int autotune_batch(msc_ctx* c, int prec, const std::vector<BSys>& sys, const std::vector<BOp>& ops,
-                          int nslots, BatchShape& best, double& best_ms) {
+static int autotune_batch(msc_ctx* c, int prec, const BatchHost& bh, const std::vector<BSys>& sys,
+                          const std::vector<BOp>& ops, int nslots, BatchShape& best, double& best_ms) {
     const int J = (int)sys.size();
     Engine e = engine_of(c);
     BVec v = bvec_of(c, prec);
@@ -1275,27 +1403,26 @@ static int autotune_batch(msc_ctx* c, int prec, const std::vector<BSys>& sys, co
     for (int g = 0; g < nslots; ++g) c->h_slot[g].flag = 2;
     CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * J, cudaMemcpyHostToDevice, c->work));
     CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
+    std::vector<int> all(J);
+    for (int j = 0; j < J; ++j) all[j] = j;
     const int site_c[] = {64, 128, 256};
     const int vec_c[][2] = {{256, 1}, {256, 2}, {256, 4}, {128, 4}};
     cudaEvent_t e0 = c->prof[0], e1 = c->prof[1];
     best_ms = 1e30;
-    int st = MSC_OK;
     for (int si : site_c) {
         for (auto& vc : vec_c) {
             BatchShape sh;
             sh.site_threads = si;
             sh.vec_threads = vc[0];
             sh.units = vc[1];
-            BatchDev bd;
-            st = upload_batch_tables(c, sys, ops, sh, prec, bd);
+            int st = set_active(c, bh, sys, ops, all, sh, prec);
             if (st == MSC_ERR_UNSUPPORTED) continue;  // a system needs more blocks than a row holds
             if (st) return st;
             float ms = 0;
             for (int rep = 0; rep < 4; ++rep) {
                 if (rep == 1) CK(cudaEventRecord(e0, c->work));
-                CK(launch_b_stag(prec, PASS_A, 0, e, dsec(c, D_K1), bd.sys, bd.ops, bd.msite, J, bd.nsite,
-                                 sh.site_threads, c->work));
-                CK(launch_b_update(prec, sh.units, e, v, bd.sys, bd.mupd, J, bd.nupd, sh.vec_threads, c->work));
+                CK(launch_b_stag(prec, PASS_A, 0, e, dsec(c, D_K1), bh.tab, sh.site_threads, c->work));
+                CK(launch_b_update(prec, sh.units, e, v, bh.tab, sh.vec_threads, c->work));
             }
             CK(cudaEventRecord(e1, c->work));
             CK(cudaEventSynchronize(e1));
@@ -1449,7 +1576,12 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
         hsec(c, D_RUC)[j] = ru_pass(mkdesc(t64j, xb, bj, rj, d0[j], j, j, FIN_SETR));
         slot0 += q.S;
     }
-    // ---- autotuned launch shape ------------------------------------------------
+    // ---- tables and autotuned launch shape -------------------------------------
+    BatchHost bh;
+    st = batch_layout(c, std::max(J, nslots), nprob, bh);
+    if (st) return st;
+    st = upload_systems(c, bh, sys, ops);
+    if (st) return st;
     BatchShape shape;
     double tuned_ms = 0.0;
     int tuned_now = 0;
@@ -1474,7 +1606,7 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
             shape = hit.first;
             tuned_ms = hit.second;
         } else {
-            st = autotune_batch(c, prec, sys, ops, nslots, shape, tuned_ms);
+            st = autotune_batch(c, prec, bh, sys, ops, nslots, shape, tuned_ms);
             if (st) return st;
             tuned_now = 1;
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1491,16 +1623,17 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
     CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * J, cudaMemcpyHostToDevice, c->work));
     CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
     for (int sct : {D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, sct, J));
-    BatchDev bd;
-    st = upload_batch_tables(c, sys, ops, shape, prec, bd);
+    std::vector<int> all(J);
+    for (int j = 0; j < J; ++j) all[j] = j;
+    st = set_active(c, bh, sys, ops, all, shape, prec);
     if (st) return st;
     Engine e = engine_of(c);
     BVec v = bvec_of(c, prec);
-    CK(launch_b_init(prec, e, v, bd.sys, bd.mvec, J, bd.nvec, shape.vec_threads, c->work));
+    CK(launch_b_init(prec, e, v, bh.tab, shape.vec_threads, c->work));
     c->launches++;
     const int chunk = 25;
     int rel = 0, rel_ref = 0;
-    st = run_stage_b(c, prec, J, chunk, mixed, bd, shape, prm.max_iter, &rel);
+    st = run_stage_b(c, prec, J, chunk, mixed, bh, sys, ops, shape, prm.max_iter, &rel);
     if (st) return st;
     std::vector<int> sys_status(J, MSC_OK), sys_iters(J, 0);
     std::vector<double> bnorm2(J);
@@ -1512,7 +1645,9 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
         else if (q.status == ST_ERR_NONFINITE) sys_status[j] = MSC_ERR_NONFINITE;
     }
     if (mixed) {
-        CK(launch_b_fold(e, v, bd.sys, bd.mvec, J, bd.nvec, shape.vec_threads, 0, c->work));
+        st = set_active(c, bh, sys, ops, all, shape, prec);
+        if (st) return st;
+        CK(launch_b_fold(e, v, bh.tab, shape.vec_threads, 0, c->work));
         c->launches++;
     }
     CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslots, cudaMemcpyDeviceToHost, c->work));
@@ -1558,13 +1693,15 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
         CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * m, cudaMemcpyHostToDevice, c->work));
         CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
         for (int sct : {D_RIA, D_RIC, D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, sct, m));
-        BatchDev rd;
-        st = upload_batch_tables(c, rs, ops, shape, prec, rd);
+        CK(cudaStreamSynchronize(c->work));
+        st = upload_systems(c, bh, rs, ops);
         if (st) return st;
-        CK(launch_b_stag(PREC_F64, PASS_A, 0, e, dsec(c, D_RIA), rd.sys, rd.ops, rd.msite, m, rd.nsite,
-                         shape.site_threads, c->work));
-        CK(launch_b_stag(PREC_F64, PASS_C, mixed ? 1 : 0, e, dsec(c, D_RIC), rd.sys, rd.ops, rd.msite, m,
-                         rd.nsite, shape.site_threads, c->work));
+        std::vector<int> rall(m);
+        for (int k = 0; k < m; ++k) rall[k] = k;
+        st = set_active(c, bh, rs, ops, rall, shape, prec);
+        if (st) return st;
+        CK(launch_b_stag(PREC_F64, PASS_A, 0, e, dsec(c, D_RIA), bh.tab, shape.site_threads, c->work));
+        CK(launch_b_stag(PREC_F64, PASS_C, mixed ? 1 : 0, e, dsec(c, D_RIC), bh.tab, shape.site_threads, c->work));
         c->launches += 2;
         CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * m, cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
@@ -1577,9 +1714,9 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
             else if (q.status == ST_RUNNING) next.push_back(g);
         }
         if (check_only || next.empty()) break;
-        CK(launch_b_init_from_r(prec, e, v, rd.sys, rd.mvec, m, rd.nvec, shape.vec_threads, c->work));
+        CK(launch_b_init_from_r(prec, e, v, bh.tab, shape.vec_threads, c->work));
         c->launches++;
-        st = run_stage_b(c, prec, m, chunk, mixed, rd, shape, prm.max_iter, &rel_ref);
+        st = run_stage_b(c, prec, m, chunk, mixed, bh, rs, ops, shape, prm.max_iter, &rel_ref);
         if (st) return st;
         int most = 0;
         for (int k = 0; k < m; ++k) {
@@ -1593,7 +1730,9 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
         ref_total += most;
         rounds++;
         if (mixed) {
-            CK(launch_b_fold(e, v, rd.sys, rd.mvec, m, rd.nvec, shape.vec_threads, 0, c->work));
+            st = set_active(c, bh, rs, ops, rall, shape, prec);
+            if (st) return st;
+            CK(launch_b_fold(e, v, bh.tab, shape.vec_threads, 0, c->work));
             c->launches++;
         }
         todo.clear();

@@ -115,17 +115,25 @@ struct BVec {            // base pointers of the batch's vectors
     double2* t64;
     const double2* b64;
 };
+struct BTab {             // device tables of a batched stage
+    const BSys* sys;     // [systems]
+    const BOp* ops;      // [operators]
+    const int* hdr;      // {active systems, site, vector, update virtual blocks}
+    const int* act;      // [active] system indices
+    const int* msite;    // [active + 1] prefix sums of blocks: operator passes
+    const int* mvec;     // [active + 1] one unit per thread (init, fold)
+    const int* mupd;     // [active + 1] `units` units per thread (update)
+};
 cudaError_t launch_b_stag(int prec, int kind, int out_f32, const Engine& e, const PassDesc* descs,
-                          const BSys* sys, const BOp* ops, const int* map, int J, int nblk, int threads,
+                          const BTab& t, int threads, cudaStream_t st);
+cudaError_t launch_b_init(int prec, const Engine& e, const BVec& v, const BTab& t, int threads,
                           cudaStream_t st);
-cudaError_t launch_b_init(int prec, const Engine& e, const BVec& v, const BSys* sys, const int* map,
-                          int J, int nblk, int threads, cudaStream_t st);
-cudaError_t launch_b_init_from_r(int prec, const Engine& e, const BVec& v, const BSys* sys,
-                                 const int* map, int J, int nblk, int threads, cudaStream_t st);
-cudaError_t launch_b_update(int prec, int units, const Engine& e, const BVec& v, const BSys* sys,
-                            const int* map, int J, int nblk, int threads, cudaStream_t st);
-cudaError_t launch_b_fold(const Engine& e, const BVec& v, const BSys* sys, const int* map, int J,
-                          int nblk, int threads, int only_ru, cudaStream_t st);
+cudaError_t launch_b_init_from_r(int prec, const Engine& e, const BVec& v, const BTab& t, int threads,
+                                 cudaStream_t st);
+cudaError_t launch_b_update(int prec, int units, const Engine& e, const BVec& v, const BTab& t, int threads,
+                            cudaStream_t st);
+cudaError_t launch_b_fold(const Engine& e, const BVec& v, const BTab& t, int threads, int only_ru,
+                          cudaStream_t st);
 
 // adjoint (force.cu)
 cudaError_t launch_quad(const Engine& e, const double2* phi, const double2* x, const double* c, int S,
