@@ -7,6 +7,8 @@
 // a warp's loads of values and column indices are contiguous 256/128-byte
 // runs. Rows shorter than the slice's longest row are padded with zero
 // blocks pointing at column 0.
+#include <algorithm>
+
 #include "engine.h"
 
 namespace msc {
@@ -88,15 +90,16 @@ __device__ __forceinline__ void bsr_row(const OpDev& A, const T2<T>* __restrict_
 // row loop is latency-bound and wants every resident warp).
 template <class T, int BD, int KIND, class TO>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1)
-k_bsr(Engine e, const PassDesc* descs, OpDev A, const T2<T>* __restrict__ vals) {
-    const PassDesc d = descs[blockIdx.y];
+k_bsr(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A, const T2<T>* __restrict__ vals) {
+    const SysBlock q = sys_block(npass, act);
+    if (!q.ok) return;
+    const PassDesc d = descs[q.j];
     if (gated_off(e, d)) return;
     const T2<T>* __restrict__ src = (const T2<T>*)d.src;
     const T2<T>* __restrict__ aux = (const T2<T>*)d.aux;
     const T dd = (T)d.d;
     double local = 0.0;
-    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.nbr;
-         row += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t row = q.bx * (int64_t)blockDim.x + threadIdx.x; row < A.nbr; row += (int64_t)q.gx * blockDim.x) {
         T2<T> y[BD];
         bsr_row<T, BD>(A, vals, src, row, y);
         if (KIND == PASS_A) {  // out = (A + d) src, P term = Re src^dag out
@@ -135,7 +138,7 @@ k_bsr(Engine e, const PassDesc* descs, OpDev A, const T2<T>* __restrict__ vals) 
     }
     if (d.row >= 0) {
         double tot;
-        if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
+        if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize(e, d, tot);
     }
 }
 
@@ -147,15 +150,19 @@ k_bsr(Engine e, const PassDesc* descs, OpDev A, const T2<T>* __restrict__ vals) 
 // act[1..] their indices, so that groups stay full as systems finish.
 template <class T, int BD, int G>
 __global__ void __launch_bounds__(kThreads, G >= 8 ? 2 : (G >= 4 ? 3 : (G >= 2 ? 4 : 5)))
-k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A,
+k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int groups, OpDev A,
             const T2<T>* __restrict__ vals) {
     __shared__ PassDesc sd[G];
     __shared__ unsigned s_mask;
     if (threadIdx.x == 0) s_mask = 0u;
     __syncthreads();
+    // groups are interleaved in blockIdx.x: the blocks of every group for the
+    // same rows run together, so each matrix tile is read from DRAM once and
+    // from L2 by the other groups
+    const int grp = blockIdx.x % groups, bx = blockIdx.x / groups, gx = gridDim.x / groups;
     if (threadIdx.x < G) {
         const int na = act ? __ldg(act) : npass;
-        const int j = blockIdx.y * G + threadIdx.x;
+        const int j = grp * G + threadIdx.x;
         if (j < na) {
             sd[threadIdx.x] = descs[act ? __ldg(act + 1 + j) : j];
             if (!gated_off(e, sd[threadIdx.x])) atomicOr(&s_mask, 1u << threadIdx.x);
@@ -167,8 +174,7 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A,
     double local[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) local[g] = 0.0;
-    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.nbr;
-         row += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t row = bx * (int64_t)blockDim.x + threadIdx.x; row < A.nbr; row += (int64_t)gx * blockDim.x) {
         const int64_t slice = row >> 5;
         const int lane = (int)(row & 31);
         const int len = __ldg(&A.slice_len[slice]);
@@ -223,28 +229,28 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A,
     for (int g = 0; g < G; ++g) {
         if (!((mask >> g) & 1u) || sd[g].row < 0) continue;
         double tot;
-        if (reduce_last(e, sd[g].row, local[g], tot)) finalize(e, sd[g], tot);
+        if (reduce_last_n(e, sd[g].row, local[g], tot, gx, bx)) finalize(e, sd[g], tot);
     }
 }
 
 template <class T, int BD, int KIND, class TO>
 static void launch_one(const Engine& e, const PassDesc* descs, const OpDev& A, const T2<T>* vals,
-                       int npass, cudaStream_t st) {
+                       int npass, const int* act, bool per, cudaStream_t st) {
     auto k = k_bsr<T, BD, KIND, TO>;
-    dim3 grid(resident_grid((const void*)k, A.nbr), npass);
-    k<<<grid, kThreads, 0, st>>>(e, descs, A, vals);
+    k<<<multi_grid((const void*)k, A.nbr, npass, per), kThreads, 0, st>>>(e, descs, npass, act, A, vals);
 }
 
 template <class T, int BD>
 static cudaError_t launch_bd(int kind, int out_f32, const Engine& e, const PassDesc* descs,
-                             const OpDev& A, const T2<T>* vals, int npass, cudaStream_t st) {
+                             const OpDev& A, const T2<T>* vals, int npass, const int* act, bool per,
+                             cudaStream_t st) {
     switch (kind) {
-        case PASS_A: launch_one<T, BD, PASS_A, T>(e, descs, A, vals, npass, st); break;
+        case PASS_A: launch_one<T, BD, PASS_A, T>(e, descs, A, vals, npass, act, per, st); break;
         case PASS_C:
-            if (out_f32) launch_one<T, BD, PASS_C, float>(e, descs, A, vals, npass, st);
-            else launch_one<T, BD, PASS_C, double>(e, descs, A, vals, npass, st);
+            if (out_f32) launch_one<T, BD, PASS_C, float>(e, descs, A, vals, npass, act, per, st);
+            else launch_one<T, BD, PASS_C, double>(e, descs, A, vals, npass, act, per, st);
             break;
-        case PASS_D: launch_one<T, BD, PASS_D, T>(e, descs, A, vals, npass, st); break;
+        case PASS_D: launch_one<T, BD, PASS_D, T>(e, descs, A, vals, npass, act, per, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -254,8 +260,9 @@ template <int BD, int G>
 static void launch_multi_g(const Engine& e, const PassDesc* descs, int npass, const int* act, int groups,
                            const OpDev& A, cudaStream_t st) {
     auto k = k_bsr_multi<float, BD, G>;
-    dim3 grid(resident_grid((const void*)k, A.nbr), groups);
-    k<<<grid, kThreads, 0, st>>>(e, descs, npass, act, A, A.vals32);
+    // row blocks interleaved with groups in x
+    const int nb = std::max(1, resident_grid((const void*)k, A.nbr) / groups);
+    k<<<nb * groups, kThreads, 0, st>>>(e, descs, npass, act, groups, A, A.vals32);
 }
 
 template <int BD>
@@ -280,21 +287,21 @@ cudaError_t launch_bsr_multi(const OpDev& op, const Engine& e, const PassDesc* d
 }
 
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
-                            const PassDesc* d_descs, int npass, cudaStream_t st) {
-    if (kind == PASS_A && npass > 1 && prec == PREC_F32)
-        return launch_bsr_multi(op, e, d_descs, npass, nullptr, 8, (npass + 7) / 8, st);
+                            const PassDesc* d_descs, int npass, cudaStream_t st, const int* act, bool per) {
+    if (kind == PASS_A && npass > 1 && prec == PREC_F32 && !per)
+        return launch_bsr_multi(op, e, d_descs, npass, act, 8, (npass + 7) / 8, st);
     if (prec == PREC_F64) {
         switch (op.bd) {
-            case 1: return launch_bd<double, 1>(kind, out_f32, e, d_descs, op, op.vals64, npass, st);
-            case 2: return launch_bd<double, 2>(kind, out_f32, e, d_descs, op, op.vals64, npass, st);
-            default: return launch_bd<double, 3>(kind, out_f32, e, d_descs, op, op.vals64, npass, st);
+            case 1: return launch_bd<double, 1>(kind, out_f32, e, d_descs, op, op.vals64, npass, act, per, st);
+            case 2: return launch_bd<double, 2>(kind, out_f32, e, d_descs, op, op.vals64, npass, act, per, st);
+            default: return launch_bd<double, 3>(kind, out_f32, e, d_descs, op, op.vals64, npass, act, per, st);
         }
     }
     if (kind == PASS_C) return cudaErrorInvalidValue;
     switch (op.bd) {
-        case 1: return launch_bd<float, 1>(kind, out_f32, e, d_descs, op, op.vals32, npass, st);
-        case 2: return launch_bd<float, 2>(kind, out_f32, e, d_descs, op, op.vals32, npass, st);
-        default: return launch_bd<float, 3>(kind, out_f32, e, d_descs, op, op.vals32, npass, st);
+        case 1: return launch_bd<float, 1>(kind, out_f32, e, d_descs, op, op.vals32, npass, act, per, st);
+        case 2: return launch_bd<float, 2>(kind, out_f32, e, d_descs, op, op.vals32, npass, act, per, st);
+        default: return launch_bd<float, 3>(kind, out_f32, e, d_descs, op, op.vals32, npass, act, per, st);
     }
 }
 

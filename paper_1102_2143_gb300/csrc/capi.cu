@@ -210,13 +210,17 @@ static PassDesc ru_pass(PassDesc d) {
     return d;
 }
 
+// per_system: a whole grid per pass (passes only some systems need:
+// reliable updates, FP64 residual checks); otherwise the passes share one
+// grid over the active list `act` (see sys_block).
 static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int out_f32, int sec,
-                           int npass, const Engine* eng = nullptr) {
+                           int npass, const Engine* eng = nullptr, const int* act = nullptr,
+                           bool per_system = false) {
     Engine e = eng ? *eng : engine_of(c);
     c->launches++;
     if (A.kind == OP_STAGGERED)
-        return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work);
-    return launch_bsr_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work);
+        return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work, act, per_system);
+    return launch_bsr_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work, act, per_system);
 }
 
 
@@ -228,6 +232,7 @@ static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys,
                                  int& kernels) {
     Engine e = engine_of(c);
     VecSet v = vecs_of(c, prec, npad);
+    const int* act = (const int*)c->actb.p;
     kernels = 0;
     for (int it = 0; it < chunk; ++it) {
         const bool prof = profile && it == 0;
@@ -235,30 +240,30 @@ static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys,
         cudaError_t err;
         if (group > 0) {
             c->launches++;
-            err = launch_bsr_multi(A, e, dsec(c, D_K1), nsys, (const int*)c->actb.p, group, groups, c->work);
+            err = launch_bsr_multi(A, e, dsec(c, D_K1), nsys, act, group, groups, c->work);
         } else {
-            err = op_pass(c, A, prec, PASS_A, 0, D_K1, nsys);
+            err = op_pass(c, A, prec, PASS_A, 0, D_K1, nsys, &e, act);
         }
         if (err != cudaSuccess) return err;
         if (prof) cudaEventRecordWithFlags(c->prof[1], c->work, cudaEventRecordExternal);
-        if (A.kind == OP_STAGGERED) err = op_pass(c, A, prec, PASS_B, 0, D_K2, nsys);
-        else err = launch_axpy_norm(prec, e, v, dsec(c, D_K2), nsys, c->work);
+        if (A.kind == OP_STAGGERED) err = op_pass(c, A, prec, PASS_B, 0, D_K2, nsys, &e, act);
+        else err = launch_axpy_norm(prec, e, v, dsec(c, D_K2), nsys, c->work, act);
         if (err != cudaSuccess) return err;
         if (prof) cudaEventRecordWithFlags(c->prof[2], c->work, cudaEventRecordExternal);
-        err = launch_update(prec, e, v, nsys, c->work);
+        err = launch_update(prec, e, v, nsys, c->work, act);
         if (err != cudaSuccess) return err;
         if (prof) cudaEventRecordWithFlags(c->prof[3], c->work, cudaEventRecordExternal);
         kernels += 3;
         if (reliable) {
-            err = launch_fold(e, v, nsys, 1, c->work);
+            err = launch_fold(e, v, nsys, 1, c->work, act, true);
             if (err != cudaSuccess) return err;
             kernels++;
             if (A.kind == OP_STAGGERED) {
-                err = op_pass(c, A, PREC_F64, PASS_A, 0, D_RUA, nsys);
+                err = op_pass(c, A, PREC_F64, PASS_A, 0, D_RUA, nsys, &e, act, true);
                 if (err != cudaSuccess) return err;
                 kernels++;
             }
-            err = op_pass(c, A, PREC_F64, PASS_C, 1, D_RUC, nsys);
+            err = op_pass(c, A, PREC_F64, PASS_C, 1, D_RUC, nsys, &e, act, true);
             if (err != cudaSuccess) return err;
             kernels++;
         }
@@ -313,17 +318,18 @@ static cudaError_t build_chunk_graph_cond(msc_ctx* c, const OpDev& A, int prec, 
         const bool prof = profile && it == 0;
         if (it == 0) err = cudaMemsetAsync(flags, 0, sizeof(int) * chunk, c->work);
         if (prof) cudaEventRecordWithFlags(c->prof[0], c->work, cudaEventRecordExternal);
+        const int* act = (const int*)c->actb.p;
         if (err == cudaSuccess) {
-            if (group > 0) err = launch_bsr_multi(A, e, dsec(c, D_K1), nsys, (const int*)c->actb.p, group, groups, c->work);
-            else err = op_pass(c, A, prec, PASS_A, 0, D_K1, nsys, &e);
+            if (group > 0) err = launch_bsr_multi(A, e, dsec(c, D_K1), nsys, act, group, groups, c->work);
+            else err = op_pass(c, A, prec, PASS_A, 0, D_K1, nsys, &e, act);
         }
         if (prof) cudaEventRecordWithFlags(c->prof[1], c->work, cudaEventRecordExternal);
         if (err == cudaSuccess) {
-            if (A.kind == OP_STAGGERED) err = op_pass(c, A, prec, PASS_B, 0, D_K2, nsys, &e2);
-            else err = launch_axpy_norm(prec, e2, v, dsec(c, D_K2), nsys, c->work);
+            if (A.kind == OP_STAGGERED) err = op_pass(c, A, prec, PASS_B, 0, D_K2, nsys, &e2, act);
+            else err = launch_axpy_norm(prec, e2, v, dsec(c, D_K2), nsys, c->work, act);
         }
         if (prof) cudaEventRecordWithFlags(c->prof[2], c->work, cudaEventRecordExternal);
-        if (err == cudaSuccess) err = launch_update(prec, e, v, nsys, c->work);
+        if (err == cudaSuccess) err = launch_update(prec, e, v, nsys, c->work, act);
         if (prof) cudaEventRecordWithFlags(c->prof[3], c->work, cudaEventRecordExternal);
         kernels += 3;
         cudaError_t et = capture_tail(c->work, tail);
@@ -342,9 +348,9 @@ static cudaError_t build_chunk_graph_cond(msc_ctx* c, const OpDev& A, int prec, 
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         err = begin_capture_into(c->work, body, {});
         if (err != cudaSuccess) break;
-        err = launch_fold(e, v, nsys, 1, c->work);
-        if (err == cudaSuccess && A.kind == OP_STAGGERED) err = op_pass(c, A, PREC_F64, PASS_A, 0, D_RUA, nsys, &e);
-        if (err == cudaSuccess) err = op_pass(c, A, PREC_F64, PASS_C, 1, D_RUC, nsys, &e);
+        err = launch_fold(e, v, nsys, 1, c->work, act, true);
+        if (err == cudaSuccess && A.kind == OP_STAGGERED) err = op_pass(c, A, PREC_F64, PASS_A, 0, D_RUA, nsys, &e, act, true);
+        if (err == cudaSuccess) err = op_pass(c, A, PREC_F64, PASS_C, 1, D_RUC, nsys, &e, act, true);
         ee = cudaStreamEndCapture(c->work, &gg);
         if (err == cudaSuccess) err = ee;
         tail.assign(1, ifn);
@@ -421,8 +427,9 @@ struct ProfAcc {
 static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk, bool reliable,
                      bool profile, int64_t npad, int max_iter, ProfAcc* pa, int* rel_updates,
                      bool compact = false) {
+    // group sizes of the shared-matrix SpMV follow the number still iterating
     compact = compact && op->dev.kind == OP_BSR && prec == PREC_F32 && nsys > 1;
-    if (compact) {
+    {
         bool moved = false;
         CK(grow(c->actb, sizeof(int) * (nsys + 1), moved));
         if (moved) c->gen++;
@@ -435,7 +442,10 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
     GraphEntry* ge = nullptr;
     int st = MSC_OK;
     if (!compact) {
-        st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, 0, 0, &ge);
+        // nsys > 1 block-CSR stages without regrouping keep groups of 8
+        const bool multi = op->dev.kind == OP_BSR && prec == PREC_F32 && nsys > 1;
+        st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, multi ? 8 : 0,
+                       multi ? (nsys + 7) / 8 : 0, &ge);
         if (st != MSC_OK) return st;
     }
     CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost, c->work));
@@ -447,15 +457,14 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
         for (int j = 0; j < nsys; ++j) {
             if (c->h_sys[j].status < ST_DONE) any = true;
             if (c->h_sys[j].status != ST_RUNNING) all_running = false;
-            else if (compact) c->h_act[1 + active++] = j;
+            else c->h_act[1 + active++] = j;
         }
         if (!any) break;
+        c->h_act[0] = active;
+        CK(cudaMemcpyAsync(c->actb.p, c->h_act, sizeof(int) * (active + 1), cudaMemcpyHostToDevice, c->work));
         if (compact) {
             const int group = active <= 1 ? 1 : (active <= 2 ? 2 : (active <= 4 ? 4 : 8));
             const int groups = (active + group - 1) / group;
-            c->h_act[0] = active;
-            CK(cudaMemcpyAsync(c->actb.p, c->h_act, sizeof(int) * (active + 1), cudaMemcpyHostToDevice,
-                               c->work));
             st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, group, groups, &ge);
             if (st != MSC_OK) return st;
         }
@@ -1033,8 +1042,8 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
             CK(cudaMemcpyAsync(c->sys.p, c->h_sys, sizeof(SysScalars) * m, cudaMemcpyHostToDevice, c->work));
             CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
             for (int s : {D_RIA, D_RIC, D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, s, m));
-            if (A.kind == OP_STAGGERED) CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_RIA, m));
-            CK(op_pass(c, A, PREC_F64, PASS_C, mixed ? 1 : 0, D_RIC, m));
+            if (A.kind == OP_STAGGERED) CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_RIA, m, nullptr, nullptr, true));
+            CK(op_pass(c, A, PREC_F64, PASS_C, mixed ? 1 : 0, D_RIC, m, nullptr, nullptr, true));
             CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * m, cudaMemcpyDeviceToHost, c->work));
             CK(cudaStreamSynchronize(c->work));
             std::vector<int> next;

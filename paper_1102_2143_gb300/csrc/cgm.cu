@@ -15,9 +15,11 @@ namespace msc {
 // r = b (in iteration precision), p = r, p_s = r (non-base shifts), x = 0;
 // reduction |b|^2 in FP64 from the FP64 source.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_init(Engine e, VecSet v, const PassDesc* descs) {
+__global__ void __launch_bounds__(kThreads) k_init(Engine e, VecSet v, const PassDesc* descs, int nsys) {
     using V = typename U16<T>::t;
-    const PassDesc d = descs[blockIdx.y];
+    const SysBlock q = sys_block(nsys, nullptr);
+    if (!q.ok) return;
+    const PassDesc d = descs[q.j];
     const int j = d.sys;
     const SysScalars* s = &e.sys[j];
     const int S = s->S, base = s->base, slot0 = s->slot0, rhs = s->rhs;
@@ -29,8 +31,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Engine e, VecSet v, const Pas
     const double2* b = v.b64 + (size_t)rhs * v.npad;
     double local = 0.0;
     const V zero = {};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = q.bx * (int64_t)blockDim.x + threadIdx.x; i < upv; i += (int64_t)q.gx * blockDim.x) {
         V rv;
         if constexpr (U16<T>::cpu == 2) {
             double2 b0 = b[2 * i], b1 = b[2 * i + 1];
@@ -56,15 +57,17 @@ __global__ void __launch_bounds__(kThreads) k_init(Engine e, VecSet v, const Pas
         }
     }
     double tot;
-    if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
+    if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize(e, d, tot);
 }
 
 // p = r, p_s = r, x accumulator of the system's shifts = 0 (start of a solve
 // whose residual r was just computed from a warm start).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_init_from_r(Engine e, VecSet v) {
+__global__ void __launch_bounds__(kThreads) k_init_from_r(Engine e, VecSet v, int nsys) {
     using V = typename U16<T>::t;
-    const int j = blockIdx.y;
+    const SysBlock q = sys_block(nsys, nullptr);
+    if (!q.ok) return;
+    const int j = q.j;
     const SysScalars* s = &e.sys[j];
     if (load_status(s) != ST_RUNNING) return;
     const int S = s->S, base = s->base, slot0 = s->slot0;
@@ -75,8 +78,7 @@ __global__ void __launch_bounds__(kThreads) k_init_from_r(Engine e, VecSet v) {
     V* xit = (V*)v.xit;
     const V zero = {};
     const bool mixed = (void*)v.xit != (void*)v.x64;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = q.bx * (int64_t)blockDim.x + threadIdx.x; i < upv; i += (int64_t)q.gx * blockDim.x) {
         const V rv = r[i];
         p[i] = rv;
         for (int k = 0; k < S; ++k) {
@@ -96,10 +98,12 @@ __global__ void __launch_bounds__(kThreads) k_init_from_r(Engine e, VecSet v) {
 constexpr int kUnits = 4;
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v) {
+__global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v, int nsys, const int* act) {
     using V = typename U16<T>::t;
     constexpr int U = kUnits;
-    const int j = blockIdx.y;
+    const SysBlock qb = sys_block(nsys, act);
+    if (!qb.ok) return;
+    const int j = qb.j;
     SysScalars* s = &e.sys[j];
     const int st = load_status(s);
     if (st != ST_RUNNING && st != ST_FINISHING) return;
@@ -120,8 +124,8 @@ __global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v) {
     V* __restrict__ p = (V*)v.p + (size_t)j * upv;
     V* __restrict__ ps = (V*)v.ps + (size_t)slot0 * upv;
     V* __restrict__ xs = (V*)v.xit + (size_t)slot0 * upv;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < upv; i0 += step * U) {
+    const int64_t step = (int64_t)qb.gx * blockDim.x;
+    for (int64_t i0 = qb.bx * (int64_t)blockDim.x + threadIdx.x; i0 < upv; i0 += step * U) {
         V rv[U], pv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -169,17 +173,20 @@ __global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v) {
             if (i < upv) p[i] = axpy(beta, pv[u], rv[u]);
         }
     }
-    if (arrive_last(e, j)) {
+    if (arrive_last_n(e, j, qb.gx)) {
         if (threadIdx.x == 0 && s->status == ST_FINISHING) s->status = ST_DONE;
     }
 }
 
 // Block-CSR path: r -= alpha Ap and R' = |r|^2 (Algorithm 1, lines 20 and 24).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, const PassDesc* descs) {
+__global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, const PassDesc* descs, int nsys,
+                                                        const int* act) {
     using V = typename U16<T>::t;
     constexpr int U = kUnits;
-    const PassDesc d = descs[blockIdx.y];
+    const SysBlock sb = sys_block(nsys, act);
+    if (!sb.ok) return;
+    const PassDesc d = descs[sb.j];
     if (gated_off(e, d)) return;
     const int j = d.sys;
     const T na = -(T)e.sys[j].alpha;
@@ -187,8 +194,8 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, cons
     V* __restrict__ r = (V*)v.r + (size_t)j * upv;
     const V* __restrict__ ap = (const V*)v.t + (size_t)j * upv;
     double local = 0.0;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < upv; i0 += step * U) {
+    const int64_t step = (int64_t)sb.gx * blockDim.x;
+    for (int64_t i0 = sb.bx * (int64_t)blockDim.x + threadIdx.x; i0 < upv; i0 += step * U) {
         V rv[U], av[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -209,13 +216,15 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, cons
         }
     }
     double tot;
-    if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
+    if (reduce_last_n(e, d.row, local, tot, sb.gx, sb.bx)) finalize(e, d, tot);
 }
 
 // x_s(FP64) += x_s(FP32 accumulator); accumulator = 0, for every shift of
 // the system (mixed precision; runs whatever the system's status).
-__global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v, int only_ru) {
-    const int j = blockIdx.y;
+__global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v, int only_ru, int nsys, const int* act) {
+    const SysBlock sb = sys_block(nsys, act);
+    if (!sb.ok) return;
+    const int j = sb.j;
     const SysScalars* s = &e.sys[j];
     const int st = load_status(s);
     if (st == ST_ERR_NOT_HPD || st == ST_ERR_NONFINITE) return;
@@ -223,8 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v, int only_
     const int S = s->S, slot0 = s->slot0;
     const int64_t upv = v.npad / 2;
     float4* xa = (float4*)v.xit;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < upv;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = sb.bx * (int64_t)blockDim.x + threadIdx.x; i < upv; i += (int64_t)sb.gx * blockDim.x) {
         for (int k = 0; k < S; ++k) {
             const size_t g = (size_t)(slot0 + k);
             const float4 dx = xa[g * upv + i];
@@ -287,41 +295,50 @@ int resident_grid(const void* fn, int64_t work) {
     return (int)b;
 }
 
-template <class K>
-static dim3 vgrid(K kernel, int64_t upv, int units_per_thread, int nsys) {
-    return dim3(resident_grid((const void*)kernel, (upv + units_per_thread - 1) / units_per_thread), nsys);
+dim3 multi_grid(const void* fn, int64_t work, int nsys, bool per_system) {
+    if (per_system && nsys > 1) return dim3(resident_grid(fn, work), nsys);
+    // enough blocks for all systems' work, capped at the resident blocks,
+    // never fewer than one block per system
+    const int64_t total = work * std::max(nsys, 1);
+    return dim3(std::max(resident_grid(fn, total), std::max(nsys, 1)));
 }
 
 static int64_t upv_of(int prec, const VecSet& v) { return prec == PREC_F32 ? v.npad / 2 : v.npad; }
 
+template <class K>
+static dim3 vgrid(K kernel, int64_t upv, int units_per_thread, int nsys, bool per_system = false) {
+    return multi_grid((const void*)kernel, (upv + units_per_thread - 1) / units_per_thread, nsys, per_system);
+}
+
 cudaError_t launch_init(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
                         int nsys, cudaStream_t st) {
-    if (prec == PREC_F32) k_init<float><<<vgrid(k_init<float>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs);
-    else k_init<double><<<vgrid(k_init<double>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs);
+    if (prec == PREC_F32) k_init<float><<<vgrid(k_init<float>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys);
+    else k_init<double><<<vgrid(k_init<double>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st) {
-    if (prec == PREC_F32) k_init_from_r<float><<<vgrid(k_init_from_r<float>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v);
-    else k_init_from_r<double><<<vgrid(k_init_from_r<double>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v);
+    if (prec == PREC_F32) k_init_from_r<float><<<vgrid(k_init_from_r<float>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, nsys);
+    else k_init_from_r<double><<<vgrid(k_init_from_r<double>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, nsys);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st) {
-    if (prec == PREC_F32) k_update<float><<<vgrid(k_update<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v);
-    else k_update<double><<<vgrid(k_update<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v);
+cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st, const int* act) {
+    if (prec == PREC_F32) k_update<float><<<vgrid(k_update<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, nsys, act);
+    else k_update<double><<<vgrid(k_update<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, nsys, act);
     return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
-                             int nsys, cudaStream_t st) {
-    if (prec == PREC_F32) k_axpy_norm<float><<<vgrid(k_axpy_norm<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs);
-    else k_axpy_norm<double><<<vgrid(k_axpy_norm<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs);
+                             int nsys, cudaStream_t st, const int* act) {
+    if (prec == PREC_F32) k_axpy_norm<float><<<vgrid(k_axpy_norm<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys, act);
+    else k_axpy_norm<double><<<vgrid(k_axpy_norm<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys, act);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int only_ru, cudaStream_t st) {
-    k_fold<<<vgrid(k_fold, v.npad / 2, 1, nsys), kThreads, 0, st>>>(e, v, only_ru);
+cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int only_ru, cudaStream_t st, const int* act,
+                        bool per_system) {
+    k_fold<<<vgrid(k_fold, v.npad / 2, 1, nsys, per_system), kThreads, 0, st>>>(e, v, only_ru, nsys, act);
     return cudaGetLastError();
 }
 

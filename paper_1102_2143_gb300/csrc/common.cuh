@@ -382,6 +382,47 @@ __device__ __forceinline__ void finalize(const Engine& e, const PassDesc& d, dou
     }
 }
 
+// Which system a block serves. Kernels over several systems use a 1-D grid
+// whose blocks are dealt round-robin to the systems of the list `act`
+// ({count, indices}, in device memory, rewritten by the host between graph
+// launches) or to all `nsys` systems when act is null: block b serves system
+// act[1 + b % count] as its block b / count of gridDim.x / count. Systems of
+// one operator thus run side by side (shared matrix and link tiles are read
+// from DRAM once), and as systems finish the same grid spreads over fewer.
+struct SysBlock {
+    int j;     // system
+    int bx;    // block within the system
+    int gx;    // blocks of the system
+    bool ok;   // false: this block has no work
+};
+
+//
+// A 2-D grid instead gives every system a whole grid row (blockIdx.y = system):
+// used by passes that only some listed systems need (reliable updates, FP64
+// checks), where the others' blocks exit at once and the busy ones keep the
+// full device.
+__device__ __forceinline__ SysBlock sys_block(int nsys, const int* act) {
+    SysBlock s;
+    if (gridDim.y > 1 || !act) {
+        if (gridDim.y > 1) {
+            s.j = blockIdx.y;
+            s.bx = blockIdx.x;
+            s.gx = gridDim.x;
+            s.ok = s.j < nsys;
+            return s;
+        }
+    }
+    const int na = act ? __ldg(act) : nsys;
+    s.ok = na > 0;
+    if (!s.ok) { s.j = s.bx = s.gx = 0; return s; }
+    const int k = blockIdx.x % na;
+    s.bx = blockIdx.x / na;
+    s.gx = gridDim.x / na;
+    s.ok = s.bx < s.gx;
+    s.j = act ? __ldg(act + 1 + k) : k;
+    return s;
+}
+
 // Gate at kernel entry: true if this pass has nothing to do.
 __device__ __forceinline__ bool gated_off(const Engine& e, const PassDesc& d) {
     if (d.sys < 0) return false;

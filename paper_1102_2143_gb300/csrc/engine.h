@@ -44,10 +44,15 @@ struct OpDev {
 };
 
 // kernel launchers (return the launch error)
+// `act` (device, optional): {count, indices} of the passes to run (see
+// sys_block in common.cuh); null runs all npass.
+// per_system: one whole grid row per pass (see sys_block).
 cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
-                             const PassDesc* d_descs, int npass, cudaStream_t st);
+                             const PassDesc* d_descs, int npass, cudaStream_t st, const int* act = nullptr,
+                             bool per_system = false);
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
-                            const PassDesc* d_descs, int npass, cudaStream_t st);
+                            const PassDesc* d_descs, int npass, cudaStream_t st, const int* act = nullptr,
+                            bool per_system = false);
 // FP32 SpMV of several systems sharing the matrix, `group` (1, 2, 4, 8)
 // systems per block row of the grid, `groups` rows; `act` (device, optional)
 // = {count, indices...} of the systems to run, read when the kernel runs.
@@ -69,10 +74,12 @@ struct VecSet {
 cudaError_t launch_init(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
                         int nsys, cudaStream_t st);
 cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st);
-cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st);
+cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st,
+                          const int* act = nullptr);
 cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
-                             int nsys, cudaStream_t st);
-cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int only_ru, cudaStream_t st);
+                             int nsys, cudaStream_t st, const int* act = nullptr);
+cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int only_ru, cudaStream_t st,
+                        const int* act = nullptr, bool per_system = false);
 cudaError_t launch_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n,
                            cudaStream_t st);
 
@@ -148,5 +155,9 @@ int grid_blocks(int64_t work, int num_sms);
 // Blocks of kThreads for `work` items: one item per thread, capped at the
 // blocks that fit on the device at once for kernel `fn` (no partial waves).
 int resident_grid(const void* fn, int64_t work);
+// Grid for `nsys` systems of `work` items each (see sys_block): 1-D, the
+// resident blocks and at least one per system; or, per_system, a full row
+// of resident blocks for every system.
+dim3 multi_grid(const void* fn, int64_t work, int nsys, bool per_system = false);
 
 }  // namespace msc

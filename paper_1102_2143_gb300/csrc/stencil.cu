@@ -13,62 +13,67 @@
 // ([mu][component][site]) so that a warp's link loads are contiguous. In
 // FP32, SU(3) links keep two rows (third = conj(row0 x row1)) and SU(2)
 // links keep one row (second = (-conj u01, conj u00)).
+#include <algorithm>
+
 #include "stencil.cuh"
 
 namespace msc {
 
-// One D pass over every site with the epilogue `KIND` (see PASS_* in engine.h).
+// One D pass over every site with the epilogue `KIND` (see PASS_* in engine.h),
+// for the systems of the pass list (see sys_block in common.cuh).
 template <class T, int NC, int RECON, int KIND, class TO>
-__global__ void __launch_bounds__(kThreads) k_stag(Engine e, const PassDesc* descs, StagGeom g,
-                                                   const void* links) {
-    const PassDesc d = descs[blockIdx.y];
+__global__ void __launch_bounds__(kThreads) k_stag(Engine e, const PassDesc* descs, int npass, const int* act,
+                                                   StagGeom g, const void* links) {
+    const SysBlock q = sys_block(npass, act);
+    if (!q.ok) return;
+    const PassDesc d = descs[q.j];
     if (gated_off(e, d)) return;
     const T alpha = KIND == PASS_B ? (T)e.sys[d.sys].alpha : T(0);
     double local = 0.0;
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.V; x += gridDim.x * blockDim.x)
+    for (int x = q.bx * blockDim.x + threadIdx.x; x < g.V; x += q.gx * blockDim.x)
         local += stag_site<T, NC, RECON, KIND, TO>(d, g, links, alpha, x);
     if (d.row >= 0) {
         double tot;
-        if (reduce_last(e, d.row, local, tot)) finalize(e, d, tot);
+        if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize(e, d, tot);
     }
 }
 
 template <class T, int NC, int RECON, int KIND, class TO>
 static void launch_one(const Engine& e, const PassDesc* descs, StagGeom g, const void* links, int npass,
-                       cudaStream_t st) {
+                       const int* act, bool per, cudaStream_t st) {
     auto k = k_stag<T, NC, RECON, KIND, TO>;
-    dim3 grid(resident_grid((const void*)k, g.V), npass);
-    k<<<grid, kThreads, 0, st>>>(e, descs, g, links);
+    k<<<multi_grid((const void*)k, g.V, npass, per), kThreads, 0, st>>>(e, descs, npass, act, g, links);
 }
 
 template <class T, int NC, int RECON>
 static cudaError_t launch_kind(int kind, int out_f32, const Engine& e, const PassDesc* descs,
-                               StagGeom g, const void* links, int npass, cudaStream_t st) {
+                               StagGeom g, const void* links, int npass, const int* act, bool per,
+                               cudaStream_t st) {
     switch (kind) {
-        case PASS_A: launch_one<T, NC, RECON, PASS_A, T>(e, descs, g, links, npass, st); break;
-        case PASS_B: launch_one<T, NC, RECON, PASS_B, T>(e, descs, g, links, npass, st); break;
+        case PASS_A: launch_one<T, NC, RECON, PASS_A, T>(e, descs, g, links, npass, act, per, st); break;
+        case PASS_B: launch_one<T, NC, RECON, PASS_B, T>(e, descs, g, links, npass, act, per, st); break;
         case PASS_C:
-            if (out_f32) launch_one<T, NC, RECON, PASS_C, float>(e, descs, g, links, npass, st);
-            else launch_one<T, NC, RECON, PASS_C, double>(e, descs, g, links, npass, st);
+            if (out_f32) launch_one<T, NC, RECON, PASS_C, float>(e, descs, g, links, npass, act, per, st);
+            else launch_one<T, NC, RECON, PASS_C, double>(e, descs, g, links, npass, act, per, st);
             break;
-        default: launch_one<T, NC, RECON, PASS_D, T>(e, descs, g, links, npass, st); break;
+        default: launch_one<T, NC, RECON, PASS_D, T>(e, descs, g, links, npass, act, per, st); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
-                             const PassDesc* d_descs, int npass, cudaStream_t st) {
+                             const PassDesc* d_descs, int npass, cudaStream_t st, const int* act, bool per) {
     if (prec == PREC_F64) {
-        if (op.nc == 3) return launch_kind<double, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links64, npass, st);
-        return launch_kind<double, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links64, npass, st);
+        if (op.nc == 3) return launch_kind<double, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links64, npass, act, per, st);
+        return launch_kind<double, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links64, npass, act, per, st);
     }
     if (kind == PASS_C) return cudaErrorInvalidValue;  // residual passes run in FP64
     if (op.nc == 3) {
-        if (op.recon) return launch_kind<float, 3, 1>(kind, out_f32, e, d_descs, op.g, op.links32, npass, st);
-        return launch_kind<float, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links32, npass, st);
+        if (op.recon) return launch_kind<float, 3, 1>(kind, out_f32, e, d_descs, op.g, op.links32, npass, act, per, st);
+        return launch_kind<float, 3, 0>(kind, out_f32, e, d_descs, op.g, op.links32, npass, act, per, st);
     }
-    if (op.recon) return launch_kind<float, 2, 1>(kind, out_f32, e, d_descs, op.g, op.links32, npass, st);
-    return launch_kind<float, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links32, npass, st);
+    if (op.recon) return launch_kind<float, 2, 1>(kind, out_f32, e, d_descs, op.g, op.links32, npass, act, per, st);
+    return launch_kind<float, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links32, npass, act, per, st);
 }
 
 // ---------------------------------------------------------------------------
