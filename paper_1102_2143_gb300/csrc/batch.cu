@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kThreads) kb_stag(Engine e, const PassDesc* de
         const PassDesc d = descs[q.j];
         if (gated_off(e, d)) continue;
         const BOp op = t.ops[t.sys[q.j].op];
-        const T alpha = KIND == PASS_B ? (T)e.sys[d.sys].alpha : T(0);
+        const T alpha = (KIND == PASS_B || KIND == PASS_BC) ? (T)e.sys[d.sys].alpha : T(0);
         double local = 0.0;
         const int x = q.lb * blockDim.x + threadIdx.x;
         if (x < op.g.V) {
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kThreads) kb_stag(Engine e, const PassDesc* de
         }
         if (d.row >= 0) {
             double tot;
-            if (reduce_last_n(e, d.row, local, tot, q.nb, q.lb)) finalize(e, d, tot);
+            if (reduce_last_n(e, d.row, local, tot, q.nb, q.lb)) finalize<KIND == PASS_BC>(e, d, tot);
         }
     }
 }
@@ -304,7 +304,10 @@ cudaError_t launch_b_stag(int prec, int kind, int out_f32, const Engine& e, cons
     if (prec == PREC_F64) {
         switch (kind) {
             case PASS_A: launch_bs<double, PASS_A, double>(e, descs, t, threads, st); break;
-            case PASS_B: launch_bs<double, PASS_B, double>(e, descs, t, threads, st); break;
+            case PASS_B:
+                if (e.cond_flag) launch_bs<double, PASS_BC, double>(e, descs, t, threads, st);
+                else launch_bs<double, PASS_B, double>(e, descs, t, threads, st);
+                break;
             case PASS_C:
                 if (out_f32) launch_bs<double, PASS_C, float>(e, descs, t, threads, st);
                 else launch_bs<double, PASS_C, double>(e, descs, t, threads, st);
@@ -314,7 +317,10 @@ cudaError_t launch_b_stag(int prec, int kind, int out_f32, const Engine& e, cons
     } else {
         switch (kind) {
             case PASS_A: launch_bs<float, PASS_A, float>(e, descs, t, threads, st); break;
-            case PASS_B: launch_bs<float, PASS_B, float>(e, descs, t, threads, st); break;
+            case PASS_B:
+                if (e.cond_flag) launch_bs<float, PASS_BC, float>(e, descs, t, threads, st);
+                else launch_bs<float, PASS_B, float>(e, descs, t, threads, st);
+                break;
             default: return cudaErrorInvalidValue;
         }
     }

@@ -87,9 +87,10 @@ __device__ __forceinline__ void bsr_row(const OpDev& A, const T2<T>* __restrict_
 }
 
 // FP32: at most 48 registers, so that five 256-thread blocks fit an SM (the
-// row loop is latency-bound and wants every resident warp).
+// row loop is latency-bound and wants every resident warp); FP64: three
+// blocks at most 80 registers each: no spills, enough warps for the FP64 pipe.
 template <class T, int BD, int KIND, class TO>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 3)
 k_bsr(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A, const T2<T>* __restrict__ vals) {
     const SysBlock q = sys_block(npass, act);
     if (!q.ok) return;

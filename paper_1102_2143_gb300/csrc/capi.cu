@@ -1326,8 +1326,12 @@ static cudaError_t build_chunk_graph_b_cond(msc_ctx* c, int prec, int chunk, con
 static int get_graph_b(msc_ctx* c, int prec, int chunk, bool reliable, const BTab& t, const BatchShape& sh,
                        GraphEntry** out) {
     char key[200];
-    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%p", prec, chunk, (int)reliable, sh.site_threads,
-             sh.vec_threads, sh.units, (const void*)t.sys);
+    // every table address is part of the key: their offsets depend on the
+    // batch's capacity
+    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p", prec, chunk, (int)reliable,
+             sh.site_threads, sh.vec_threads, sh.units, (const void*)t.sys, (const void*)t.ops,
+             (const void*)t.hdr, (const void*)t.act, (const void*)t.msite, (const void*)t.mvec,
+             (const void*)t.mupd);
     GraphEntry& ge = c->graphs[key];
     if (ge.exec && ge.gen == c->gen) {
         *out = &ge;

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_init_from_r(Engine e, VecSet v, in
 constexpr int kUnits = 4;
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v, int nsys, const int* act) {
+__global__ void __launch_bounds__(kThreads, 2) k_update(Engine e, VecSet v, int nsys, const int* act) {
     using V = typename U16<T>::t;
     constexpr int U = kUnits;
     const SysBlock qb = sys_block(nsys, act);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Engine e, VecSet v, int nsy
 }
 
 // Block-CSR path: r -= alpha Ap and R' = |r|^2 (Algorithm 1, lines 20 and 24).
-template <class T>
+template <class T, bool COND>
 __global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, const PassDesc* descs, int nsys,
                                                         const int* act) {
     using V = typename U16<T>::t;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, cons
         }
     }
     double tot;
-    if (reduce_last_n(e, d.row, local, tot, sb.gx, sb.bx)) finalize(e, d, tot);
+    if (reduce_last_n(e, d.row, local, tot, sb.gx, sb.bx)) finalize<COND>(e, d, tot);
 }
 
 // x_s(FP64) += x_s(FP32 accumulator); accumulator = 0, for every shift of
@@ -331,8 +331,13 @@ cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, 
 
 cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
                              int nsys, cudaStream_t st, const int* act) {
-    if (prec == PREC_F32) k_axpy_norm<float><<<vgrid(k_axpy_norm<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys, act);
-    else k_axpy_norm<double><<<vgrid(k_axpy_norm<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys, act);
+    if (prec == PREC_F32) {
+        if (e.cond_flag) k_axpy_norm<float, true><<<vgrid(k_axpy_norm<float, true>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys, act);
+        else k_axpy_norm<float, false><<<vgrid(k_axpy_norm<float, false>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys, act);
+    } else {
+        if (e.cond_flag) k_axpy_norm<double, true><<<vgrid(k_axpy_norm<double, true>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys, act);
+        else k_axpy_norm<double, false><<<vgrid(k_axpy_norm<double, false>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys, act);
+    }
     return cudaGetLastError();
 }
 

@@ -272,6 +272,10 @@ __device__ __forceinline__ void fin_P(const Engine& e, int j, double P) {
     if (threadIdx.x == 0) { s->P = P; s->alpha = alpha; }
 }
 
+// COND: this kernel runs inside a chunk graph with conditional update nodes
+// and sets the iteration's condition (a separate instance, so that kernels
+// launched elsewhere contain no graph call and stay profilable).
+template <bool COND>
 __device__ __forceinline__ void fin_R(const Engine& e, int j, double Rn) {
     SysScalars* s = &e.sys[j];
     const double R = s->R, alpha = s->alpha;
@@ -315,8 +319,10 @@ __device__ __forceinline__ void fin_R(const Engine& e, int j, double Rn) {
         const int ru = (s->ru_every > 0 && s->status == ST_RUNNING &&
                         (Rn <= s->delta2 * Rmax || since >= s->ru_every)) ? 1 : 0;
         s->ru = ru;
-        if (ru && e.cond_flag && atomicExch(e.cond_flag, 1) == 0)
-            cudaGraphSetConditional((cudaGraphConditionalHandle)e.cond, 1u);
+        if constexpr (COND) {
+            if (ru && e.cond_flag && atomicExch(e.cond_flag, 1) == 0)
+                cudaGraphSetConditional((cudaGraphConditionalHandle)e.cond, 1u);
+        }
     }
 }
 
@@ -370,10 +376,11 @@ __device__ __forceinline__ void fin_init(const Engine& e, int j, double b2) {
     }
 }
 
+template <bool COND = false>
 __device__ __forceinline__ void finalize(const Engine& e, const PassDesc& d, double total) {
     switch (d.fin) {
         case FIN_P: fin_P(e, d.sys, total); break;
-        case FIN_R: fin_R(e, d.sys, total); break;
+        case FIN_R: fin_R<COND>(e, d.sys, total); break;
         case FIN_SETR: fin_setR(e, d.sys, total, false); break;
         case FIN_SETR_INIT: fin_setR(e, d.sys, total, true); break;
         case FIN_INIT: fin_init(e, d.sys, total); break;

@@ -15,6 +15,7 @@ enum {
     PASS_B = 1,  // staggered: r -= alpha (d aux - D src); reduce |r|^2
     PASS_C = 2,  // out = b - (d aux - D src) | b - (A+d) src; reduce |out|^2
     PASS_D = 3,  // out = d aux - D src | (A+d) src
+    PASS_BC = 4, // PASS_B inside a conditional chunk graph (sets the update condition)
 };
 
 struct StagGeom {

@@ -28,13 +28,13 @@ __global__ void __launch_bounds__(kThreads) k_stag(Engine e, const PassDesc* des
     if (!q.ok) return;
     const PassDesc d = descs[q.j];
     if (gated_off(e, d)) return;
-    const T alpha = KIND == PASS_B ? (T)e.sys[d.sys].alpha : T(0);
+    const T alpha = (KIND == PASS_B || KIND == PASS_BC) ? (T)e.sys[d.sys].alpha : T(0);
     double local = 0.0;
     for (int x = q.bx * blockDim.x + threadIdx.x; x < g.V; x += q.gx * blockDim.x)
         local += stag_site<T, NC, RECON, KIND, TO>(d, g, links, alpha, x);
     if (d.row >= 0) {
         double tot;
-        if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize(e, d, tot);
+        if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize<KIND == PASS_BC>(e, d, tot);
     }
 }
 
@@ -51,7 +51,10 @@ static cudaError_t launch_kind(int kind, int out_f32, const Engine& e, const Pas
                                cudaStream_t st) {
     switch (kind) {
         case PASS_A: launch_one<T, NC, RECON, PASS_A, T>(e, descs, g, links, npass, act, per, st); break;
-        case PASS_B: launch_one<T, NC, RECON, PASS_B, T>(e, descs, g, links, npass, act, per, st); break;
+        case PASS_B:
+            if (e.cond_flag) launch_one<T, NC, RECON, PASS_BC, T>(e, descs, g, links, npass, act, per, st);
+            else launch_one<T, NC, RECON, PASS_B, T>(e, descs, g, links, npass, act, per, st);
+            break;
         case PASS_C:
             if (out_f32) launch_one<T, NC, RECON, PASS_C, float>(e, descs, g, links, npass, act, per, st);
             else launch_one<T, NC, RECON, PASS_C, double>(e, descs, g, links, npass, act, per, st);

@@ -138,7 +138,7 @@ __device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g
             }
         }
         return (double)loc;
-    } else if (KIND == PASS_B) {
+    } else if (KIND == PASS_B || KIND == PASS_BC) {
         T2<T>* r = (T2<T>*)d.out;
         T loc = T(0);
 #pragma unroll
