@@ -46,7 +46,7 @@ __device__ __forceinline__ VBlock vblock(const BTab& t, const int* map, int vb) 
 }
 
 template <class T, int KIND, class TO>
-__global__ void __launch_bounds__(kThreads) kb_stag(Engine e, const PassDesc* descs, BTab t) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) kb_stag(Engine e, const PassDesc* descs, BTab t) {
     const int total = __ldg(t.hdr + 1);
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         const VBlock q = vblock(t, t.msite, vb);

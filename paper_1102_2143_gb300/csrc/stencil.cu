@@ -21,9 +21,16 @@ namespace msc {
 
 // One D pass over every site with the epilogue `KIND` (see PASS_* in engine.h),
 // for the systems of the pass list (see sys_block in common.cuh).
+// FP32 passes: at most 80 registers (three 256-thread blocks per SM); the
+// site loop is bound by the latency of its link and neighbour loads, and
+// more resident warps beat the loads the compiler would otherwise hoist
+// (32^4 solve: 1.81 s uncapped, 1.51 s at three blocks, 1.55 s at four).
+#ifndef MSC_STAG_MINB
+#define MSC_STAG_MINB 3
+#endif
 template <class T, int NC, int RECON, int KIND, class TO>
-__global__ void __launch_bounds__(kThreads) k_stag(Engine e, const PassDesc* descs, int npass, const int* act,
-                                                   StagGeom g, const void* links) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? MSC_STAG_MINB : 1)
+k_stag(Engine e, const PassDesc* descs, int npass, const int* act, StagGeom g, const void* links) {
     const SysBlock q = sys_block(npass, act);
     if (!q.ok) return;
     const PassDesc d = descs[q.j];
