@@ -39,6 +39,37 @@ WORKLOAD = "24^4 SU(3) staggered A=M^dag M as block-CSR, 15 shifts 1e-4..10, 1 R
 L2_BYTES = 129 * 2 ** 20
 
 
+SPMV_COUNTERS = os.path.join(ROOT, "profiles", "bsr_spmv_24x4_counters.md")
+SPMV_SOURCES = ("common.cuh", "engine.h", "bsr.cu")
+
+
+def spmv_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in SPMV_SOURCES:
+        with open(os.path.join(ROOT, "paper_1102_2143_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def load_spmv_traffic():
+    """DRAM bytes (read + write) of one FP32 block-CSR SpMV launch on this
+    workload, from the committed ncu counter summary; None when the kernel's
+    sources changed after the counters were taken."""
+    try:
+        vals = {}
+        with open(SPMV_COUNTERS) as f:
+            for line in f:
+                m = line.strip().strip("`").split(":", 1)
+                if len(m) == 2:
+                    vals[m[0].strip()] = m[1].strip()
+        if vals.get("kernel_sources_sha256") != spmv_source_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -293,6 +324,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the device-timed steps with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -341,11 +375,15 @@ def main():
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
+    if args.profile_region:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     for _ in range(args.steps):
         infos.append(step(b_dev, x_dev))
     ev1.record(stream)
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.profiler.stop()
     barrier(pg, torch)
     clk = clocks.stop()
     ms_local = ev0.elapsed_time(ev1) / args.steps
@@ -364,7 +402,7 @@ def main():
     if spmv_ms:
         ach = spmv_b / (spmv_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "kernel": "k_bsr<float,3,PASS_A> (SpMV + fused P)",
+                "traffic": load_spmv_traffic(), "kernel": "k_bsr<float,3,PASS_A> (SpMV + fused P)",
                 "bytes_per_launch": spmv_b, "launch_ms": spmv_ms, "peak_source": peak_kind,
                 "update_kernel_ms": float(np.mean([i.update_ms for i in infos])),
                 "rupdate_kernel_ms": float(np.mean([i.rupdate_ms for i in infos]))}
