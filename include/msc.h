@@ -93,7 +93,9 @@ int msc_op_staggered(msc_ctx* ctx, msc_op** op, int nc, const int dims[4],
  * col_idx[nnzb] (int32 in [0, nbr)), vals[nnzb][bd][bd] complex FP64.
  * Repeated block columns in a row add. A must be Hermitian positive
  * definite; this is not checked here (the solve reports MSC_ERR_NOT_HPD
- * when it meets p^dagger A p <= 0). n = nbr * bd. */
+ * when it meets p^dagger A p <= 0). n = nbr * bd. A block row may hold
+ * at most 2^26 / (bd * bd) blocks (about 7.4 million 3 x 3 blocks);
+ * longer rows, like any other malformed input, give MSC_ERR_ARG. */
 int msc_op_bsr(msc_ctx* ctx, msc_op** op, int64_t nbr, int bd, const int64_t* row_ptr,
                const int32_t* col_idx, const double* vals, unsigned flags);
 

@@ -59,26 +59,27 @@ cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
     return cudaGetLastError();
 }
 
-// y = A src for one row (thread = row, lanes of a warp = rows of a slice)
+// y = A src for one row (thread = row, lanes of a warp = rows of a slice).
+// Slice bases are 64-bit; offsets inside a slice (k * 32 * BD * BD) stay
+// 32-bit; the source gathers go through the read-only path.
 template <class T, int BD>
 __device__ __forceinline__ void bsr_row(const OpDev& A, const T2<T>* __restrict__ vals,
-                                        const T2<T>* __restrict__ src, int64_t row,
-                                        T2<T> (&y)[BD]) {
-    const int64_t slice = row >> 5;
-    const int lane = (int)(row & 31);
+                                        const T2<T>* __restrict__ src, int row, T2<T> (&y)[BD]) {
+    const int slice = row >> 5;
+    const int lane = row & 31;
     const int len = __ldg(&A.slice_len[slice]);
     const int64_t st = __ldg(&A.slice_start[slice]);
 #pragma unroll
     for (int a = 0; a < BD; ++a) y[a] = {T(0), T(0)};
-    const int32_t* cp = A.cols + st * 32 + lane;
-    const T2<T>* vp = vals + st * BD * BD * 32 + lane;
+    const int32_t* __restrict__ cp = A.cols + st * 32 + lane;
+    const T2<T>* __restrict__ vp = vals + st * BD * BD * 32 + lane;
 #pragma unroll 3
     for (int k = 0; k < len; ++k) {
-        const int c = __ldg(cp + (size_t)k * 32);
+        const int c = __ldg(cp + k * 32);
         T2<T> xv[BD];
 #pragma unroll
-        for (int b = 0; b < BD; ++b) xv[b] = src[(size_t)c * BD + b];
-        const T2<T>* vk = vp + (size_t)k * BD * BD * 32;
+        for (int b = 0; b < BD; ++b) xv[b] = __ldg(src + (size_t)c * BD + b);
+        const T2<T>* vk = vp + k * (BD * BD * 32);
 #pragma unroll
         for (int a = 0; a < BD; ++a)
 #pragma unroll
@@ -86,11 +87,12 @@ __device__ __forceinline__ void bsr_row(const OpDev& A, const T2<T>* __restrict_
     }
 }
 
-// FP32: at most 48 registers, so that five 256-thread blocks fit an SM (the
-// row loop is latency-bound and wants every resident warp); FP64: three
-// blocks at most 80 registers each: no spills, enough warps for the FP64 pipe.
+// FP32: four 256-thread blocks per SM at up to 64 registers (at five blocks
+// the 48-register cap spills and the 24^4 SpMV takes 160 us instead of
+// 150 us); FP64: three blocks at most 80 registers each: no spills, enough
+// warps for the FP64 pipe.
 template <class T, int BD, int KIND, class TO>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 3)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3)
 k_bsr(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A, const T2<T>* __restrict__ vals) {
     const SysBlock q = sys_block(npass, act);
     if (!q.ok) return;
@@ -100,7 +102,8 @@ k_bsr(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A, const
     const T2<T>* __restrict__ aux = (const T2<T>*)d.aux;
     const T dd = (T)d.d;
     double local = 0.0;
-    for (int64_t row = q.bx * (int64_t)blockDim.x + threadIdx.x; row < A.nbr; row += (int64_t)q.gx * blockDim.x) {
+    const int nbr = (int)A.nbr;
+    for (int row = q.bx * blockDim.x + threadIdx.x; row < nbr; row += q.gx * blockDim.x) {
         T2<T> y[BD];
         bsr_row<T, BD>(A, vals, src, row, y);
         if (KIND == PASS_A) {  // out = (A + d) src, P term = Re src^dag out
@@ -144,22 +147,25 @@ k_bsr(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A, const
 }
 
 // y_j = (A + d_j) src_j for up to G systems j sharing the matrix: each block
-// value and column index is read once and applied to every system of the
-// group (the refinement stage and several right-hand sides). Epilogue as
-// PASS_A, with one P reduction per system.
+// value and column index is read once per thread and applied to every system
+// of its group (the refinement stage and several right-hand sides). Epilogue
+// as PASS_A, with one P reduction per system.
+// Groups are interleaved in blockIdx.x, so the blocks of every group for the
+// same rows run together: each matrix tile comes from DRAM once and from L2
+// for the other groups. Two systems per thread is the measured optimum on
+// the 24^4 staggered pattern (14 systems: 0.45 ms at G = 2, 1.0 ms at G = 8,
+// where the 8 accumulators cost occupancy while the L2 source gathers, not
+// the matrix stream, bound the kernel).
 // `act` (optional): the passes still to run, act[0] = their count and
 // act[1..] their indices, so that groups stay full as systems finish.
 template <class T, int BD, int G>
-__global__ void __launch_bounds__(kThreads, G >= 8 ? 2 : (G >= 4 ? 3 : (G >= 2 ? 4 : 5)))
+__global__ void __launch_bounds__(kThreads, G >= 8 ? 2 : (G >= 4 ? 3 : (G >= 3 ? 4 : 5)))
 k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int groups, OpDev A,
             const T2<T>* __restrict__ vals) {
     __shared__ PassDesc sd[G];
     __shared__ unsigned s_mask;
     if (threadIdx.x == 0) s_mask = 0u;
     __syncthreads();
-    // groups are interleaved in blockIdx.x: the blocks of every group for the
-    // same rows run together, so each matrix tile is read from DRAM once and
-    // from L2 by the other groups
     const int grp = blockIdx.x % groups, bx = blockIdx.x / groups, gx = gridDim.x / groups;
     if (threadIdx.x < G) {
         const int na = act ? __ldg(act) : npass;
@@ -172,12 +178,16 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int grou
     __syncthreads();
     const unsigned mask = s_mask;
     if (!mask) return;
+    const T2<T>* srcs[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) srcs[g] = ((mask >> g) & 1u) ? (const T2<T>*)sd[g].src : nullptr;
     double local[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) local[g] = 0.0;
-    for (int64_t row = bx * (int64_t)blockDim.x + threadIdx.x; row < A.nbr; row += (int64_t)gx * blockDim.x) {
-        const int64_t slice = row >> 5;
-        const int lane = (int)(row & 31);
+    const int nbr = (int)A.nbr;
+    for (int row = bx * blockDim.x + threadIdx.x; row < nbr; row += gx * blockDim.x) {
+        const int slice = row >> 5;
+        const int lane = row & 31;
         const int len = __ldg(&A.slice_len[slice]);
         const int64_t st = __ldg(&A.slice_start[slice]);
         T2<T> acc[G][BD];
@@ -185,12 +195,12 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int grou
         for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int a = 0; a < BD; ++a) acc[g][a] = {T(0), T(0)};
-        const int32_t* cp = A.cols + st * 32 + lane;
-        const T2<T>* vp = vals + st * BD * BD * 32 + lane;
-#pragma unroll 2
+        const int32_t* __restrict__ cp = A.cols + st * 32 + lane;
+        const T2<T>* __restrict__ vp = vals + st * BD * BD * 32 + lane;
+#pragma unroll 3
         for (int k = 0; k < len; ++k) {
-            const int c = __ldg(cp + (size_t)k * 32);
-            const T2<T>* vk = vp + (size_t)k * BD * BD * 32;
+            const int c = __ldg(cp + k * 32);
+            const T2<T>* vk = vp + k * (BD * BD * 32);
             T2<T> v[BD][BD];
 #pragma unroll
             for (int a = 0; a < BD; ++a)
@@ -198,11 +208,10 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int grou
                 for (int b = 0; b < BD; ++b) v[a][b] = __ldg(vk + (a * BD + b) * 32);
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                if (!((mask >> g) & 1u)) continue;
-                const T2<T>* src = (const T2<T>*)sd[g].src;
+                if (!srcs[g]) continue;
                 T2<T> xv[BD];
 #pragma unroll
-                for (int b = 0; b < BD; ++b) xv[b] = src[(size_t)c * BD + b];
+                for (int b = 0; b < BD; ++b) xv[b] = __ldg(srcs[g] + (size_t)c * BD + b);
 #pragma unroll
                 for (int a = 0; a < BD; ++a)
 #pragma unroll
@@ -211,14 +220,13 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int grou
         }
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            if (!((mask >> g) & 1u)) continue;
-            const T2<T>* src = (const T2<T>*)sd[g].src;
+            if (!srcs[g]) continue;
             T2<T>* out = (T2<T>*)sd[g].out;
             const T dd = (T)sd[g].d;
             T loc = T(0);
 #pragma unroll
             for (int a = 0; a < BD; ++a) {
-                const T2<T> s = src[(size_t)row * BD + a];
+                const T2<T> s = __ldg(srcs[g] + (size_t)row * BD + a);
                 const T2<T> y = {acc[g][a].x + dd * s.x, acc[g][a].y + dd * s.y};
                 out[(size_t)row * BD + a] = y;
                 loc += s.x * y.x + s.y * y.y;
@@ -228,7 +236,7 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int grou
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        if (!((mask >> g) & 1u) || sd[g].row < 0) continue;
+        if (!srcs[g] || sd[g].row < 0) continue;
         double tot;
         if (reduce_last_n(e, sd[g].row, local[g], tot, gx, bx)) finalize(e, sd[g], tot);
     }
@@ -290,7 +298,8 @@ cudaError_t launch_bsr_multi(const OpDev& op, const Engine& e, const PassDesc* d
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
                             const PassDesc* d_descs, int npass, cudaStream_t st, const int* act, bool per) {
     if (kind == PASS_A && npass > 1 && prec == PREC_F32 && !per)
-        return launch_bsr_multi(op, e, d_descs, npass, act, 8, (npass + 7) / 8, st);
+        return launch_bsr_multi(op, e, d_descs, npass, act, kMultiGroup,
+                                (npass + kMultiGroup - 1) / kMultiGroup, st);
     if (prec == PREC_F64) {
         switch (op.bd) {
             case 1: return launch_bd<double, 1>(kind, out_f32, e, d_descs, op, op.vals64, npass, act, per, st);

@@ -442,10 +442,10 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
     GraphEntry* ge = nullptr;
     int st = MSC_OK;
     if (!compact) {
-        // nsys > 1 block-CSR stages without regrouping keep groups of 8
+        // nsys > 1 block-CSR stages without regrouping keep all groups
         const bool multi = op->dev.kind == OP_BSR && prec == PREC_F32 && nsys > 1;
-        st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, multi ? 8 : 0,
-                       multi ? (nsys + 7) / 8 : 0, &ge);
+        st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, multi ? kMultiGroup : 0,
+                       multi ? (nsys + kMultiGroup - 1) / kMultiGroup : 0, &ge);
         if (st != MSC_OK) return st;
     }
     CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost, c->work));
@@ -463,7 +463,7 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
         c->h_act[0] = active;
         CK(cudaMemcpyAsync(c->actb.p, c->h_act, sizeof(int) * (active + 1), cudaMemcpyHostToDevice, c->work));
         if (compact) {
-            const int group = active <= 1 ? 1 : (active <= 2 ? 2 : (active <= 4 ? 4 : 8));
+            const int group = active <= 1 ? 1 : kMultiGroup;
             const int groups = (active + group - 1) / group;
             st = get_graph(c, op, prec, nsys, chunk, reliable, profile, npad, group, groups, &ge);
             if (st != MSC_OK) return st;
@@ -721,7 +721,8 @@ int msc_op_bsr(msc_ctx* c, msc_op** out, int64_t nbr, int bd, const int64_t* row
     for (int64_t s = 0; s < nslices; ++s) {
         int64_t m = 0;
         for (int64_t i = s * 32; i < std::min(nbr, s * 32 + 32); ++i) m = std::max(m, rp[i + 1] - rp[i]);
-        if (m > (1 << 30)) return MSC_ERR_ARG;
+        // the kernels index inside a slice with 32-bit offsets (k * 32 * bd * bd)
+        if (m * 32 * bd * bd >= ((int64_t)1 << 31)) return MSC_ERR_ARG;
         slen[s] = (int32_t)m;
         sstart[s] = acc;
         acc += m;

@@ -57,6 +57,8 @@ cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, co
 // FP32 SpMV of several systems sharing the matrix, `group` (1, 2, 4, 8)
 // systems per block row of the grid, `groups` rows; `act` (device, optional)
 // = {count, indices...} of the systems to run, read when the kernel runs.
+// kMultiGroup: the group size the solver uses for two or more systems.
+constexpr int kMultiGroup = 2;
 cudaError_t launch_bsr_multi(const OpDev& op, const Engine& e, const PassDesc* d_descs, int npass,
                              const int* act, int group, int groups, cudaStream_t st);
 
