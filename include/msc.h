@@ -153,7 +153,8 @@ typedef struct {
     int max_iter;        /* cap on multi-shift iterations (and per refinement round) */
     int precision;       /* MSC_FP64 or MSC_MIXED */
     int reliable_every;  /* MSC_MIXED: FP64 reliable update at the latest after this
-                            many iterations since the last one */
+                            many iterations since the last one (4x this many in
+                            the refinement of a shift) */
     int freeze_converged;/* 1: stop updating a shift once it meets tol (default);
                             0: update every shift until all meet tol */
     int refine;          /* max refinement rounds after the multi-shift solve
