@@ -313,6 +313,57 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# the paper's own workload (Sec. 4, Table 1), context beside the headline
+# ----------------------------------------------------------------------------
+
+PAPER_T10 = {  # ms per iteration, Table 1 (2-D Poisson, 1000 x 1000, 15 shifts)
+    "hardware": "one T10 GPU of an NVIDIA Tesla S1070; CPU: Intel Nehalem 2.67 GHz, one core",
+    "cgm_15_shifts_gpu_fp64": 12.9839, "cgm_15_shifts_gpu_fp32": 8.82461,
+    "cg_unshifted_gpu_fp64": 3.48276, "cg_unshifted_gpu_fp32": 2.20814,
+    "cg_unshifted_cpu_fp64": 159.158,
+}
+
+
+def paper_workload(ctx, msc, inputs, torch, stream):
+    """The 1000 x 1000 five-point Poisson operator with 15 shifts through the
+    generic block-CSR path (1 x 1 blocks): time to solution and ms per
+    multi-shift iteration, FP64 and mixed, and the single unshifted system,
+    beside the paper's T10 numbers. Complex arithmetic: the Gaussian source
+    is complex, so each iteration carries two real right-hand sides' worth
+    of vectors (the matrix is read once)."""
+    p = inputs.poisson_2d_15shifts()
+    op = msc.msc_op_bsr(ctx, p.n, 1, p.row_ptr, p.col_idx, p.vals)
+    b = torch.from_numpy(p.b).cuda()
+    out = {"workload": "2-D Poisson five-point, 1000x1000 (10^6 unknowns), Dirichlet; "
+                       "15 shifts log-spaced 1e-4..10; complex Gaussian source; tol 1e-10",
+           "paper_t10_ms_per_iteration": PAPER_T10}
+
+    def timed(sig, prec):
+        x = torch.empty((1, len(sig), p.n), dtype=torch.complex128, device="cuda")
+        msc.solve(ctx, op, b, sig, x=x, tol=p.tol, precision=prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, info = msc.solve(ctx, op, b, sig, x=x, tol=p.tol, precision=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert info.status == 0, info.status
+        ms = e0.elapsed_time(e1)
+        return {"time_to_solution_ms": ms, "iterations": info.iters,
+                "refine_iterations": info.refine_iters,
+                "ms_per_iteration": ms / max(1, info.iters + info.refine_iters),
+                "max_true_rel_resid": float(np.max(info.true_rel_resid))}
+
+    out["cgm_15_shifts_fp64"] = timed(p.sigma, msc.MSC_FP64)
+    out["cgm_15_shifts_mixed"] = timed(p.sigma, msc.MSC_MIXED)
+    out["cg_unshifted_fp64"] = timed(np.array([0.0]), msc.MSC_FP64)
+    out["cgm_15_fp64_speedup_per_iteration_vs_t10"] = (
+        PAPER_T10["cgm_15_shifts_gpu_fp64"] / out["cgm_15_shifts_fp64"]["ms_per_iteration"])
+    msc.msc_op_destroy(op)
+    return out
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 
@@ -323,6 +374,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-paper", action="store_true",
+                    help="skip the paper's own 2-D Poisson workload (context numbers)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the device-timed steps with cudaProfilerStart/Stop "
@@ -436,6 +489,10 @@ def main():
             "value": fp64_solve_bytes(finfos[-1], S, nnzb, bd, n) / (f_ms * 1e-3) / 1e9,
             "unit": "GB/s", "spmv_fp64_launch_ms": finfos[-1].op_ms}
 
+    paper = None
+    if rank == 0 and not args.no_paper:
+        paper = paper_workload(ctx, msc, inputs, torch, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_line(p, nnzb, bd, n, S, iters=6)
@@ -459,6 +516,7 @@ def main():
             "max_true_rel_resid": float(np.max(last.true_rel_resid)),
             "fp64_plain": fp64, "speedup_vs_fp64_plain": f_ms / ms,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+            "paper_workload": paper,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

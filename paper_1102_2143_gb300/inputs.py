@@ -125,6 +125,57 @@ def random_hpd_bsr(nbr: int, bd: int, blocks_per_row: int, shift: float, seed: i
             np.asarray(vals, dtype=np.complex128).reshape(-1, bd, bd), A)
 
 
+def poisson_5pt_bsr(N: int):
+    """The 2-D Poisson operator of Sec. 4: the five-point finite-difference
+    Laplacian on an N x N grid (Dirichlet boundaries, unit spacing), as
+    block-CSR with 1 x 1 blocks. Grid point (i, j) -> row i + N j; A has 4 on
+    the diagonal and -1 for each of the up to four grid neighbours, columns
+    sorted inside a row. It is real symmetric positive definite; values are
+    returned as complex128 (imaginary parts zero) for the complex solver.
+    Returns (row_ptr int64 [N*N+1], col_idx int32 [nnz], vals [nnz][1][1]).
+    """
+    n = N * N
+    idx = np.arange(n, dtype=np.int64)
+    i, j = idx % N, idx // N
+    # neighbours in column order: (i, j-1), (i-1, j), self, (i+1, j), (i, j+1)
+    cand = [(idx - N, j > 0, -1.0), (idx - 1, i > 0, -1.0), (idx, np.ones(n, bool), 4.0),
+            (idx + 1, i < N - 1, -1.0), (idx + N, j < N - 1, -1.0)]
+    cols = np.stack([c for c, _, _ in cand], axis=1)
+    mask = np.stack([m for _, m, _ in cand], axis=1)
+    vals = np.broadcast_to(np.array([v for _, _, v in cand]), (n, 5))
+    counts = mask.sum(axis=1)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    col_idx = cols[mask].astype(np.int32)
+    v = vals[mask].astype(np.complex128).reshape(-1, 1, 1)
+    return row_ptr, col_idx, v
+
+
+@dataclass
+class PoissonProblem:
+    """The shifted family on the 2-D Poisson operator (the paper's test)."""
+    N: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    vals: np.ndarray
+    b: np.ndarray        # [n] complex128
+    sigma: np.ndarray    # [S]
+    tol: float
+
+    @property
+    def n(self) -> int:
+        return self.N * self.N
+
+
+def poisson_2d_15shifts(N: int = 1000, seed_base: int = 5000) -> PoissonProblem:
+    """N x N five-point Poisson operator, 15 shifts log-spaced 1e-4..10, a
+    complex Gaussian source (seed_base+1), tol 1e-10. The paper names 15
+    shifts and the 1000 x 1000 grid but not the shift values or the source."""
+    rp, ci, va = poisson_5pt_bsr(N)
+    b = gaussian_source(N * N, seed_base + 1)
+    return PoissonProblem(N, rp, ci, va, b, log_shifts(1e-4, 10.0, 15), 1e-10)
+
+
 @dataclass
 class StaggeredProblem:
     """One synthetic staggered shifted-family problem."""

@@ -293,6 +293,42 @@ def test_bsr_apply_and_solve_match_dense(bd):
         assert np.linalg.norm(res.x[i] - xs) <= 1e-10 * np.linalg.norm(xs)
 
 
+def _dst_solve(N, b, sigma):
+    """(A + sigma)^{-1} b for the N x N Dirichlet five-point Laplacian by its
+    eigenbasis: sin(pi k x / (N+1)) modes, eigenvalues
+    4 - 2 cos(pi k/(N+1)) - 2 cos(pi l/(N+1)) (orthonormal DST-I)."""
+    from scipy.fft import dstn, idstn
+    k = np.arange(1, N + 1)
+    lam1 = 2.0 - 2.0 * np.cos(np.pi * k / (N + 1))
+    lam = lam1[None, :] + lam1[:, None]          # [j][i] for grid row i + N j
+    B = b.reshape(N, N)
+    out = []
+    for s in sigma:
+        out.append(idstn(dstn(B, type=1, norm="ortho") / (lam + s), type=1, norm="ortho").reshape(-1))
+    return np.array(out)
+
+
+def test_poisson_operator_modes_and_solve_closed_form():
+    N = 12
+    rp, ci, va = inputs.poisson_5pt_bsr(N)
+    assert rp[-1] == 5 * N * N - 4 * N           # interior 5, edges 4, corners 3
+    # the sine modes are eigenvectors with the closed-form eigenvalues
+    x = np.arange(1, N + 1)
+    for (kx, ky) in [(1, 1), (3, 7), (N, 2)]:
+        v = np.outer(np.sin(np.pi * ky * x / (N + 1)), np.sin(np.pi * kx * x / (N + 1))).reshape(-1)
+        lam = 4 - 2 * np.cos(np.pi * kx / (N + 1)) - 2 * np.cos(np.pi * ky / (N + 1))
+        Av = oracle.bsr_apply(rp, ci, va, v.astype(np.complex128))
+        assert np.linalg.norm(Av - lam * v) <= 1e-13 * np.linalg.norm(lam * v)
+    # CG-M on the paper's operator against the spectral solution
+    b = _vec(N * N, 9)
+    sig = inputs.log_shifts(1e-4, 10.0, 15)
+    res = oracle.cgm_bsr(rp, ci, va, b, sig, 1e-13)
+    assert res.status == 0
+    want = _dst_solve(N, b.real, sig) + 1j * _dst_solve(N, b.imag, sig)
+    for s in range(len(sig)):
+        assert np.linalg.norm(res.x[s] - want[s]) <= 1e-10 * np.linalg.norm(want[s])
+
+
 def test_bsr_not_hpd_is_reported():
     rp, ci, vals, A = inputs.random_hpd_bsr(10, 2, 3, 0.5, 31)
     neg = vals.copy()
