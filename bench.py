@@ -364,6 +364,94 @@ def paper_workload(ctx, msc, inputs, torch, stream):
 
 
 # ----------------------------------------------------------------------------
+# the other hot-path workloads (secondary measurements beside the headline)
+# ----------------------------------------------------------------------------
+
+def stencil_pass_bytes(V, nc, recon):
+    """Algorithmic bytes of the two FP32 stencil passes of one iteration (one
+    right-hand side): every link once (nc-1 stored rows with reconstruction),
+    then pass 1 (t = D p, P fused) reads p and writes t, pass 2 (r -= alpha
+    (d p - D t), |r|^2 fused) reads t, p and r and writes r."""
+    link = 4 * (nc - 1 if recon else nc) * nc * 8
+    vec = nc * 8
+    return V * (link + 2 * vec), V * (link + 4 * vec)
+
+
+def other_workloads(ctx, msc, inputs, torch, stream):
+    out = {}
+    peak, _ = load_peaks()
+
+    def ev_time(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    # staggered stencil path: 32^4 SU(3), m = 0.01, eps = 0.9, 20 shifts, 1 RHS
+    p = inputs.lattice_32x4_su3_20shifts(nrhs=1)
+    V = inputs.volume(p.dims)
+    op = msc.msc_op_staggered(ctx, p.nc, p.dims, torch.from_numpy(p.links).cuda(), p.mass)
+    recon = msc.msc_op_recon(op)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.empty((1, len(p.sigma), p.n), dtype=torch.complex128, device="cuda")
+    msc.solve(ctx, op, b, p.sigma, x=x, tol=p.tol)
+    ms, (_, info) = ev_time(lambda: msc.solve(ctx, op, b, p.sigma, x=x, tol=p.tol))
+    assert info.status == 0, info.status
+    b1, b2 = stencil_pass_bytes(V, p.nc, recon)
+    out["stencil_32x4_20shifts_mixed"] = {
+        "workload": "32^4 SU(3) staggered A=M^dag M (stencil, two-row FP32 links), m=0.01, eps=0.9, "
+                    "20 shifts 1e-5..10, 1 RHS, mixed, tol 1e-10",
+        "time_to_solution_ms": ms, "iterations": info.iters, "refine_iterations": info.refine_iters,
+        "max_true_rel_resid": float(np.max(info.true_rel_resid)),
+        "pass1_ms": info.op_ms, "pass2_ms": info.rupdate_ms, "update_ms": info.update_ms,
+        "pass1_gbs": b1 / (info.op_ms * 1e-3) / 1e9, "pass2_gbs": b2 / (info.rupdate_ms * 1e-3) / 1e9,
+        "pass1_frac": b1 / (info.op_ms * 1e-3) / 1e9 / peak,
+        "pass2_frac": b2 / (info.rupdate_ms * 1e-3) / 1e9 / peak,
+        "pass_bytes": [b1, b2], "timing": "pass times: CUDA events around the pass nodes inside the solve's graphs"}
+    msc.msc_op_destroy(op)
+    del x, b
+
+    # batched uneven systems: 64 problems in one batch against one by one
+    probs = inputs.batched_uneven_systems(64)
+    ops = [msc.msc_op_staggered(ctx, q.nc, q.dims, torch.from_numpy(q.links).cuda(), q.mass)
+           for q in probs]
+    items = [(o, torch.from_numpy(q.b).cuda(), q.sigma) for o, q in zip(ops, probs)]
+    msc.solve_batched(ctx, items)
+    ms_b, (_, infos, tun) = ev_time(lambda: msc.solve_batched(ctx, items))
+    ms_s, _ = ev_time(lambda: [msc.solve(ctx, o, bb, sg) for o, bb, sg in items])
+    assert all(i.status == 0 for i in infos)
+    out["batched_64_uneven_mixed"] = {
+        "workload": "64 staggered problems, L in {4..12}, SU(2)/SU(3), m in [0.02,0.2], eps=0.6, "
+                    "4..20 shifts 1e-4..1, 4 RHS each, mixed, tol 1e-10",
+        "batched_ms": ms_b, "one_by_one_ms": ms_s, "speedup": ms_s / ms_b,
+        "tuned_shape": {"site_threads": tun.site_threads, "vec_threads": tun.vec_threads,
+                        "vec_units": tun.vec_units}}
+    for o in ops:
+        msc.msc_op_destroy(o)
+
+    # adjoint: 16^4 SU(3), 12 (sigma_s, c_s); solve, S and dS/dphi, dS/dU
+    p, c = inputs.lattice_16x4_su3_force()
+    op = msc.msc_op_staggered(ctx, p.nc, p.dims, torch.from_numpy(p.links).cuda(), p.mass)
+    phi = torch.from_numpy(p.b[0]).cuda()
+    x = torch.empty((1, len(p.sigma), p.n), dtype=torch.complex128, device="cuda")
+    dphi = torch.empty(p.n, dtype=torch.complex128, device="cuda")
+    dU = torch.empty(p.links.shape, dtype=torch.complex128, device="cuda")
+    msc.solve(ctx, op, phi, p.sigma, x=x, tol=p.tol)
+    ms_solve, _ = ev_time(lambda: msc.solve(ctx, op, phi, p.sigma, x=x, tol=p.tol))
+    ms_grad, _ = ev_time(lambda: msc.msc_quad_form_grad(ctx, op, len(p.sigma), c, x[0], dphi, dU))
+    out["adjoint_16x4_12shifts"] = {
+        "workload": "16^4 SU(3), m=0.05, eps=0.7, 12 shifts 1e-4..5, c_s = sigma_s^0.5/12; "
+                    "S = sum c_s phi^dag (A+sigma_s)^-1 phi",
+        "solve_ms": ms_solve, "grad_ms": ms_grad,
+        "grad": "dS/dphi and the link force dS/dU from the solved x_s (FP64 D x_s passes + outer products)"}
+    msc.msc_op_destroy(op)
+    return out
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 
@@ -374,6 +462,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-aux", action="store_true",
+                    help="skip the secondary workloads (stencil 32^4, batched, adjoint)")
     ap.add_argument("--no-paper", action="store_true",
                     help="skip the paper's own 2-D Poisson workload (context numbers)")
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -489,6 +579,10 @@ def main():
             "value": fp64_solve_bytes(finfos[-1], S, nnzb, bd, n) / (f_ms * 1e-3) / 1e9,
             "unit": "GB/s", "spmv_fp64_launch_ms": finfos[-1].op_ms}
 
+    aux = None
+    if rank == 0 and not args.no_aux:
+        aux = other_workloads(ctx, msc, inputs, torch, stream)
+
     paper = None
     if rank == 0 and not args.no_paper:
         paper = paper_workload(ctx, msc, inputs, torch, stream)
@@ -516,7 +610,7 @@ def main():
             "max_true_rel_resid": float(np.max(last.true_rel_resid)),
             "fp64_plain": fp64, "speedup_vs_fp64_plain": f_ms / ms,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
-            "paper_workload": paper,
+            "paper_workload": paper, "other_workloads": aux,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
