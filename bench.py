@@ -545,7 +545,7 @@ def main():
     if spmv_ms:
         ach = spmv_b / (spmv_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": load_spmv_traffic(), "kernel": "k_bsr<float,3,PASS_A> (SpMV + fused P)",
+                "traffic": load_spmv_traffic(), "kernel": "k_bsr_a1<3> (FP32 SpMV + fused P)",
                 "bytes_per_launch": spmv_b, "launch_ms": spmv_ms, "peak_source": peak_kind,
                 "update_kernel_ms": float(np.mean([i.update_ms for i in infos])),
                 "rupdate_kernel_ms": float(np.mean([i.rupdate_ms for i in infos]))}

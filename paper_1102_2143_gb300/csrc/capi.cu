@@ -102,15 +102,24 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static cudaError_t grow(Buf& b, size_t bytes, bool& moved) {
+// Grows a workspace buffer (never while the work stream is capturing). The
+// new memory is zeroed on the context's work stream: the work stream is
+// non-blocking, so a cudaMemset on the legacy default stream would not be
+// ordered before the kernels that read the buffer (recycled memory then held
+// the previous owner's reduction counters and accumulators).
+static cudaError_t grow(msc_ctx* c, Buf& b, size_t bytes, bool& moved) {
     if (bytes <= b.bytes) return cudaSuccess;
-    if (b.p) cudaFree(b.p);
+    if (b.p) {
+        cudaError_t e = cudaStreamSynchronize(c->work);
+        if (e != cudaSuccess) return e;
+        cudaFree(b.p);
+    }
     b.p = nullptr;
     b.bytes = 0;
     size_t want = bytes + bytes / 8;
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) return e;
-    e = cudaMemset(b.p, 0, want);
+    e = cudaMemsetAsync(b.p, 0, want, c->work);
     if (e != cudaSuccess) return e;
     b.bytes = want;
     moved = true;
@@ -127,20 +136,20 @@ static int ensure_ws(msc_ctx* c, int64_t npad, int64_t rows, int64_t slots, int6
         moved = true;
     }
     const int64_t R = c->rows_cap;
-    CK(grow(c->sys, sizeof(SysScalars) * R, moved));
-    CK(grow(c->slot, sizeof(SlotScalars) * std::max(slots, R), moved));
-    CK(grow(c->partial, sizeof(double) * kMaxBlocks * std::max(slots, R), moved));
-    CK(grow(c->counter, sizeof(unsigned) * std::max(slots, R), moved));
-    CK(grow(c->out_red, sizeof(double) * std::max(slots, R), moved));
-    CK(grow(c->descs, sizeof(PassDesc) * D_NSECT * R, moved));
-    CK(grow(c->b64, (size_t)rhs * npad * 16, moved));
-    CK(grow(c->x64, (size_t)slots * npad * 16, moved));
-    CK(grow(c->t64, (size_t)std::max(rows, slots) * npad * 16, moved));
-    CK(grow(c->r, (size_t)R * npad * elem, moved));
-    CK(grow(c->p, (size_t)R * npad * elem, moved));
-    CK(grow(c->t, (size_t)R * npad * elem, moved));
-    CK(grow(c->ps, (size_t)slots * npad * elem, moved));
-    CK(grow(c->xit, (size_t)slots * npad * 8, moved));
+    CK(grow(c, c->sys, sizeof(SysScalars) * R, moved));
+    CK(grow(c, c->slot, sizeof(SlotScalars) * std::max(slots, R), moved));
+    CK(grow(c, c->partial, sizeof(double) * kMaxBlocks * std::max(slots, R), moved));
+    CK(grow(c, c->counter, sizeof(unsigned) * std::max(slots, R), moved));
+    CK(grow(c, c->out_red, sizeof(double) * std::max(slots, R), moved));
+    CK(grow(c, c->descs, sizeof(PassDesc) * D_NSECT * R, moved));
+    CK(grow(c, c->b64, (size_t)rhs * npad * 16, moved));
+    CK(grow(c, c->x64, (size_t)slots * npad * 16, moved));
+    CK(grow(c, c->t64, (size_t)std::max(rows, slots) * npad * 16, moved));
+    CK(grow(c, c->r, (size_t)R * npad * elem, moved));
+    CK(grow(c, c->p, (size_t)R * npad * elem, moved));
+    CK(grow(c, c->t, (size_t)R * npad * elem, moved));
+    CK(grow(c, c->ps, (size_t)slots * npad * elem, moved));
+    CK(grow(c, c->xit, (size_t)slots * npad * 8, moved));
     if (moved) c->gen++;
     const int64_t hs = std::max(slots, R);
     if (R > c->h_rows || hs > c->h_slots) {
@@ -220,7 +229,8 @@ static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int o
     c->launches++;
     if (A.kind == OP_STAGGERED)
         return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work, act, per_system);
-    return launch_bsr_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work, act, per_system);
+    return launch_bsr_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work, act, per_system,
+                           npass == 1 ? hsec(c, sec) : nullptr);
 }
 
 
@@ -295,7 +305,7 @@ static cudaError_t build_chunk_graph_cond(msc_ctx* c, const OpDev& A, int prec, 
                                           bool profile, int64_t npad, int group, int groups,
                                           cudaGraph_t* out, int& kernels) {
     bool moved = false;
-    cudaError_t err = grow(c->condf, sizeof(int) * chunk, moved);
+    cudaError_t err = grow(c, c->condf, sizeof(int) * chunk, moved);
     if (err != cudaSuccess) return err;
     if (moved) c->gen++;
     int* flags = (int*)c->condf.p;
@@ -372,9 +382,13 @@ static cudaError_t build_chunk_graph_cond(msc_ctx* c, const OpDev& A, int prec, 
 
 static int get_graph(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk, bool reliable,
                      bool profile, int64_t npad, int group, int groups, GraphEntry** out) {
-    char key[160];
-    snprintf(key, sizeof key, "%ld|%d|%d|%d|%d|%d|%lld|%d|%d", op->uid, prec, nsys, chunk, (int)reliable,
-             (int)profile, (long long)npad, group, groups);
+    // a one-system block-CSR SpMV takes its vector pointers as kernel
+    // parameters (see launch_bsr_pass): they are part of the graph's identity
+    const PassDesc& k1 = hsec(c, D_K1)[0];
+    char key[224];
+    snprintf(key, sizeof key, "%ld|%d|%d|%d|%d|%d|%lld|%d|%d|%p|%p", op->uid, prec, nsys, chunk, (int)reliable,
+             (int)profile, (long long)npad, group, groups, nsys == 1 ? k1.src : nullptr,
+             nsys == 1 ? k1.out : nullptr);
     GraphEntry& ge = c->graphs[key];
     if (ge.exec && ge.gen == c->gen) {
         *out = &ge;
@@ -431,7 +445,7 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
     compact = compact && op->dev.kind == OP_BSR && prec == PREC_F32 && nsys > 1;
     {
         bool moved = false;
-        CK(grow(c->actb, sizeof(int) * (nsys + 1), moved));
+        CK(grow(c, c->actb, sizeof(int) * (nsys + 1), moved));
         if (moved) c->gen++;
         if (c->h_act_cap < nsys + 1) {
             if (c->h_act) cudaFreeHost(c->h_act);
@@ -1156,7 +1170,7 @@ static int batch_layout(msc_ctx* c, int cap, int nops, BatchHost& bh) {
     bh.off_mu = bh.off_mv + al256(sizeof(int) * (cap + 1));
     bh.total = bh.off_mu + al256(sizeof(int) * (cap + 1));
     bool moved = false;
-    CK(grow(c->btab, bh.total, moved));
+    CK(grow(c, c->btab, bh.total, moved));
     if (moved) c->gen++;
     if (c->h_act_cap < (int64_t)(bh.total / sizeof(int)) + 1) {
         if (c->h_act) cudaFreeHost(c->h_act);
@@ -1268,7 +1282,7 @@ static cudaError_t enqueue_chunk_b(msc_ctx* c, int prec, int chunk, bool reliabl
 static cudaError_t build_chunk_graph_b_cond(msc_ctx* c, int prec, int chunk, const BTab& t,
                                             const BatchShape& sh, cudaGraph_t* out, int& kernels) {
     bool moved = false;
-    cudaError_t err = grow(c->condf, sizeof(int) * chunk, moved);
+    cudaError_t err = grow(c, c->condf, sizeof(int) * chunk, moved);
     if (err != cudaSuccess) return err;
     if (moved) c->gen++;
     int* flags = (int*)c->condf.p;
@@ -1529,20 +1543,20 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
         const int64_t R = std::max<int64_t>(c->rows_cap, 3);
         c->rows_cap = R;
         const int64_t VM = std::max(VR, VS);
-        CK(grow(c->sys, sizeof(SysScalars) * R, moved));
-        CK(grow(c->slot, sizeof(SlotScalars) * R, moved));
-        CK(grow(c->partial, sizeof(double) * kMaxBlocks * R, moved));
-        CK(grow(c->counter, sizeof(unsigned) * R, moved));
-        CK(grow(c->out_red, sizeof(double) * R, moved));
-        CK(grow(c->descs, sizeof(PassDesc) * D_NSECT * R, moved));
-        CK(grow(c->b64, (size_t)VR * 16, moved));
-        CK(grow(c->x64, (size_t)VS * 16, moved));
-        CK(grow(c->t64, (size_t)VM * 16, moved));
-        CK(grow(c->r, (size_t)VM * elem, moved));
-        CK(grow(c->p, (size_t)VM * elem, moved));
-        CK(grow(c->t, (size_t)VM * elem, moved));
-        CK(grow(c->ps, (size_t)VS * elem, moved));
-        CK(grow(c->xit, (size_t)VS * 8, moved));
+        CK(grow(c, c->sys, sizeof(SysScalars) * R, moved));
+        CK(grow(c, c->slot, sizeof(SlotScalars) * R, moved));
+        CK(grow(c, c->partial, sizeof(double) * kMaxBlocks * R, moved));
+        CK(grow(c, c->counter, sizeof(unsigned) * R, moved));
+        CK(grow(c, c->out_red, sizeof(double) * R, moved));
+        CK(grow(c, c->descs, sizeof(PassDesc) * D_NSECT * R, moved));
+        CK(grow(c, c->b64, (size_t)VR * 16, moved));
+        CK(grow(c, c->x64, (size_t)VS * 16, moved));
+        CK(grow(c, c->t64, (size_t)VM * 16, moved));
+        CK(grow(c, c->r, (size_t)VM * elem, moved));
+        CK(grow(c, c->p, (size_t)VM * elem, moved));
+        CK(grow(c, c->t, (size_t)VM * elem, moved));
+        CK(grow(c, c->ps, (size_t)VS * elem, moved));
+        CK(grow(c, c->xit, (size_t)VS * 8, moved));
         if (moved) c->gen++;
         if (R > c->h_rows || R > c->h_slots) {
             if (c->h_sys) cudaFreeHost(c->h_sys);
@@ -1817,7 +1831,7 @@ static int stage_solutions(msc_ctx* c, const msc_op* op, int S, const double* co
     int st = ensure_ws(c, npad, std::max(S, 3), S, 1, 16);
     if (st) return st;
     bool moved = false;
-    CK(grow(c->coef, sizeof(double) * S, moved));
+    CK(grow(c, c->coef, sizeof(double) * S, moved));
     CK(cudaMemcpyAsync(c->coef.p, coef, sizeof(double) * S, cudaMemcpyHostToDevice, c->work));
     CK(cudaMemcpy2DAsync(c->x64.p, npad * 16, x, n * 16, n * 16, S, cudaMemcpyDefault, c->work));
     return MSC_OK;
@@ -1871,7 +1885,7 @@ extern "C" int msc_quad_form_grad(msc_ctx* c, const msc_op* op, int S, const dou
         const bool dev_out = is_device_ptr(dU);
         if (!dev_out) {
             bool moved = false;
-            CK(grow(c->force, gbytes, moved));
+            CK(grow(c, c->force, gbytes, moved));
             G = (double2*)c->force.p;
         }
         CK(launch_force(A, x64, t64, dc, S, npad, G, c->work));

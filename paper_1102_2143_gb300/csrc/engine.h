@@ -51,9 +51,12 @@ struct OpDev {
 cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
                              const PassDesc* d_descs, int npass, cudaStream_t st, const int* act = nullptr,
                              bool per_system = false);
+// h_desc (optional): host copy of the single pass's descriptor; a one-system
+// FP32 PASS_A then takes its source and output pointers from it as kernel
+// parameters (the device descriptor must hold the same pointers).
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
                             const PassDesc* d_descs, int npass, cudaStream_t st, const int* act = nullptr,
-                            bool per_system = false);
+                            bool per_system = false, const PassDesc* h_desc = nullptr);
 // FP32 SpMV of several systems sharing the matrix, `group` (1, 2, 4, 8)
 // systems per block row of the grid, `groups` rows; `act` (device, optional)
 // = {count, indices...} of the systems to run, read when the kernel runs.
