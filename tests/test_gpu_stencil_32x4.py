@@ -9,7 +9,9 @@ At full size the oracle cannot solve the 160 systems in test time, so it
 checks what it can compute one by one: the FP64 true residual
 |b - (A + sigma_s) x_s| / |b| of sampled solutions, recomputed on the CPU
 from the returned x_s. The same recipe on an 8^4 lattice is compared with the
-oracle's own CG-M solution element by element.
+oracle's own CG-M solution element by element. A solve in a second context
+(on memory the first one freed, filled with NaN patterns in between) must
+reproduce the first bit for bit.
 
 Error bound used for x_s: A = m^2 + D^dag D with |D| <= 4 for unitary links,
 so the spectrum of A + sigma lies in [m^2 + sigma, m^2 + 16 + sigma] and
@@ -87,3 +89,29 @@ def test_32x4_recipe_on_8x4_matches_oracle_solution(ctx):
             worst = max(worst, err)
     msc.msc_op_destroy(op)
     print(f"worst x_s error {worst:.2e}")
+
+
+def test_second_context_on_recycled_memory_repeats_the_solve():
+    """Workspace zeroing must be ordered before the solve's kernels: a new
+    context whose buffers reuse freed (here NaN-filled) device memory gives
+    the same solution as the first context, bit for bit."""
+    p = inputs.lattice_32x4_su3_20shifts(L=24, nrhs=8)
+    outs = []
+    for trial in range(2):
+        c = msc.msc_create(0, torch.cuda.current_stream())
+        op = msc.msc_op_staggered(c, p.nc, p.dims, torch.from_numpy(p.links).cuda(), p.mass)
+        x, info = msc.solve(c, op, torch.from_numpy(p.b).cuda(), p.sigma, tol=p.tol,
+                            precision=msc.MSC_MIXED)
+        assert info.status == 0 and np.all(info.true_rel_resid <= p.tol)
+        outs.append((x.cpu().numpy(), info.iters, info.refine_iters))
+        msc.msc_op_destroy(op)
+        msc.msc_destroy(c)
+        del x
+        # fill what the context freed with NaN bit patterns
+        junk = torch.full((3 << 28,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        del junk
+        torch.cuda.empty_cache()
+    (x0, i0, r0), (x1, i1, r1) = outs
+    assert (i0, r0) == (i1, r1)
+    assert np.array_equal(x0, x1)
