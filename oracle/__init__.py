@@ -7,7 +7,9 @@ links or runs anything here, and this package imports nothing from it.
 The arithmetic lives in `msc_oracle.c` (plain loops, double precision); this
 module compiles it with gcc and exposes it to numpy through ctypes. Every
 function follows the paper's statement of the problem (eq. linprob, Sec. 2)
-and CG-M (Algorithm 1, Sec. 2, with the readings listed in the C file).
+and CG-M (Algorithm 1, Sec. 2, with the readings listed in the C file), and
+BiCGStab-M for non-Hermitian families (named in Sec. 1 and Sec. 3, not
+printed; its recurrences are derived in the C file's header).
 """
 from __future__ import annotations
 
@@ -25,7 +27,8 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
 
-STATUS = {0: "ok", 1: "bad argument", 4: "not HPD", 5: "non-finite", 6: "not converged"}
+STATUS = {0: "ok", 1: "bad argument", 4: "not HPD", 5: "non-finite", 6: "not converged",
+          7: "breakdown"}
 
 
 def build(force: bool = False) -> str:
@@ -71,7 +74,16 @@ def lib():
             L.orc_true_residual_staggered.argtypes = [ctypes.c_int, ip, dp, ctypes.c_double, dp,
                                                       ctypes.c_int, dp, dp, dp]
             L.orc_link_force.argtypes = [ctypes.c_int, ip, dp, ctypes.c_int, dp, dp, dp]
-            for f in ("orc_cgm_staggered", "orc_cgm_bsr", "orc_cg_staggered", "orc_cg_bsr"):
+            L.orc_bicgstabm_bsr.argtypes = [ctypes.c_long, ctypes.c_int, i64p, i32p, dp, dp,
+                                            ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, dp, ip, ip, dp, dp]
+            L.orc_bicgstabm_dirac.argtypes = [ctypes.c_int, ip, dp, ctypes.c_double, dp, ctypes.c_int,
+                                              dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, ip,
+                                              ip, dp, dp]
+            L.orc_dirac_apply_c.argtypes = [ctypes.c_int, ip, dp, ctypes.c_double, ctypes.c_double,
+                                            dp, dp]
+            for f in ("orc_cgm_staggered", "orc_cgm_bsr", "orc_cg_staggered", "orc_cg_bsr",
+                      "orc_bicgstabm_bsr", "orc_bicgstabm_dirac"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -188,6 +200,64 @@ def cgm_bsr(row_ptr, col_idx, vals, b, sigma, tol, max_iter=100000, freeze=True)
                            _dp(sig), float(tol), int(max_iter), int(bool(freeze)), _dp(x), _ip(conv),
                            _ip(it), _dp(zeta), _dp(r))
     return CGMResult(x, conv, int(it[0]), st, zeta, r)
+
+
+class BiCGStabMResult:
+    def __init__(self, x, conv_iter, iters, status, c, r):
+        self.x = x                  # [S][n]
+        self.conv_iter = conv_iter  # [S]
+        self.iters = iters
+        self.status = status
+        self.c = c                  # [S] complex zeta_sigma / T_sigma at exit
+        self.r = r                  # final seed residual
+
+
+def bicgstabm_bsr(row_ptr, col_idx, vals, b, sigma, tol, max_iter=100000, freeze=True) -> BiCGStabMResult:
+    """BiCGStab-M on a generic (non-Hermitian) block-CSR operator: all
+    (A + sigma_s) x_s = b from one BiCGStab sequence on A."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    va, b = _c128(vals), _c128(b)
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    S, n = sig.shape[0], b.shape[0]
+    x = np.zeros((S, n), dtype=np.complex128)
+    conv = np.zeros(S, dtype=np.int32)
+    it = np.zeros(1, dtype=np.int32)
+    c = np.zeros(S, dtype=np.complex128)
+    r = np.zeros(n, dtype=np.complex128)
+    st = lib().orc_bicgstabm_bsr(rp.shape[0] - 1, va.shape[-1],
+                                 rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(va), _dp(b), S,
+                                 _dp(sig), float(tol), int(max_iter), int(bool(freeze)), _dp(x),
+                                 _ip(conv), _ip(it), _dp(c), _dp(r))
+    return BiCGStabMResult(x, conv, int(it[0]), st, c, r)
+
+
+def bicgstabm_dirac(links, dims, nc, mass, b, sigma, tol, max_iter=100000, freeze=True) -> BiCGStabMResult:
+    """BiCGStab-M on the staggered Dirac operator M = m + D: the multi-mass
+    family (m + sigma_s + D) x_s = b."""
+    U, b = _c128(links), _c128(b)
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    S, n = sig.shape[0], b.shape[0]
+    x = np.zeros((S, n), dtype=np.complex128)
+    conv = np.zeros(S, dtype=np.int32)
+    it = np.zeros(1, dtype=np.int32)
+    c = np.zeros(S, dtype=np.complex128)
+    r = np.zeros(n, dtype=np.complex128)
+    d = _dims(dims)
+    st = lib().orc_bicgstabm_dirac(nc, _ip(d), _dp(U), float(mass), _dp(b), S, _dp(sig), float(tol),
+                                   int(max_iter), int(bool(freeze)), _dp(x), _ip(conv), _ip(it),
+                                   _dp(c), _dp(r))
+    return BiCGStabMResult(x, conv, int(it[0]), st, c, r)
+
+
+def dirac_apply(links, dims, nc, mass, v, sigma: float = 0.0) -> np.ndarray:
+    """(m + sigma + D) v, the staggered Dirac operator."""
+    U, v = _c128(links), _c128(v)
+    out = np.zeros_like(v)
+    d = _dims(dims)
+    lib().orc_dirac_apply_c(nc, _ip(d), _dp(U), float(mass), float(sigma), _dp(v), _dp(out))
+    return out
 
 
 def cg_staggered(links, dims, nc, mass, b, sigma, tol, max_iter=100000):

@@ -34,6 +34,31 @@
  *   - a generic block-CSR operator (complex bd x bd blocks), the generic
  *     matrix the paper's solver accepts (Sec. 3, Fig. 1).
  *
+ *   - BiCGStab-M, the multi-shift BiCGStab the paper names for
+ *     non-Hermitian families (Sec. 1, Sec. 3, Sec. 5) but does not print.
+ *     Written here in textbook BiCGStab notation (van der Vorst): seed
+ *     system A x = b with r~ = b; per iteration v = A p, alpha = rho /
+ *     (r~, v), s = r - alpha v, t = A s, omega = (t, s)/(t, t),
+ *     x += alpha p + omega s, r = s - omega t, rho' = (r~, r),
+ *     beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v).
+ *     The BiCG part of the residual polynomial obeys the same three-term
+ *     recurrence as CG's, so shifted BiCG residuals are zeta_sigma times the
+ *     seed's with the CG-M zeta recurrence; each stabilising factor is
+ *     matched by (1 - omega t) = (1 + sigma omega)(1 - omega_sigma (t + sigma)),
+ *     omega_sigma = omega / (1 + sigma omega). Then every shifted residual is
+ *     (zeta_sigma / T_sigma) r with T_sigma = prod (1 + sigma omega), and
+ *     s_sigma = (zeta'_sigma / T_sigma) s; the shifted direction update needs
+ *     (A + sigma) p_sigma = (r_sigma - s_sigma) / alpha_sigma, so no shifted
+ *     system ever applies A:
+ *       zeta'_sigma as in CG-M with the seed's alpha, beta,
+ *       alpha_sigma = alpha zeta' / zeta, beta_sigma = beta (zeta'/zeta)^2,
+ *       x_sigma += alpha_sigma p_sigma + omega_sigma s_sigma,
+ *       p_sigma = r'_sigma + beta_sigma (p_sigma
+ *                 - (omega_sigma / alpha_sigma)(r_sigma - s_sigma)).
+ *     Shift sigma is converged once |zeta_sigma / T_sigma| |r| <= tol |b|.
+ *   - the staggered Dirac operator M = m + D itself, the non-Hermitian
+ *     operator of the multi-mass family (M + sigma) x = b.
+ *
  * Parity status: every function here is pinned by tests against closed
  * forms, dense solves, textbook CG and finite differences; none is
  * "parity unpinned".
@@ -186,12 +211,22 @@ typedef struct {
 } orc_op;
 
 static long op_n(const orc_op* op) {
-    return op->kind == 0 ? vol(op->L) * op->nc : op->nbr * op->bd;
+    return op->kind != 1 ? vol(op->L) * op->nc : op->nbr * op->bd;
+}
+
+/* out = (m + sigma + D) in: the staggered Dirac operator M = m + D. */
+void orc_dirac_apply(int nc, const int L[4], const cplx* U, double mass, double sigma,
+                     const cplx* in, cplx* out) {
+    long n = vol(L) * nc;
+    orc_dslash(nc, L, U, in, out);
+    for (long i = 0; i < n; ++i) out[i] += (mass + sigma) * in[i];
 }
 
 static void op_apply(const orc_op* op, double sigma, const cplx* in, cplx* out) {
     if (op->kind == 0)
         orc_staggered_apply(op->nc, op->L, op->U, op->mass, sigma, in, out);
+    else if (op->kind == 2)
+        orc_dirac_apply(op->nc, op->L, op->U, op->mass, sigma, in, out);
     else
         orc_bsr_apply(op->nbr, op->bd, op->row_ptr, op->col_idx, op->vals, sigma, in, out);
 }
@@ -212,7 +247,8 @@ static double norm2(long n, const cplx* a) {
 /* CG-M (Algorithm 1 with readings (1)-(8))                             */
 /* ------------------------------------------------------------------ */
 
-enum { ORC_OK = 0, ORC_NOT_CONVERGED = 6, ORC_NOT_HPD = 4, ORC_NONFINITE = 5, ORC_ARG = 1 };
+enum { ORC_OK = 0, ORC_NOT_CONVERGED = 6, ORC_NOT_HPD = 4, ORC_NONFINITE = 5, ORC_ARG = 1,
+       ORC_BREAKDOWN = 7 };
 
 /*
  * x: [S][n] output. conv_iter[S] (optional): iteration at which each shift
@@ -359,6 +395,125 @@ static int cg(const orc_op* op, const cplx* b, double sigma, double tol, int max
 }
 
 /* ------------------------------------------------------------------ */
+/* BiCGStab-M (see the header for the recurrences)                     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Seed: the unshifted A (sigma = 0). x: [S][n] output. conv_iter[S]
+ * (optional). c_out[S] (optional, complex): zeta_sigma / T_sigma at exit, and
+ * r_out[n] the seed residual, so that b - (A + sigma) x_sigma =
+ * c_sigma r can be checked. tol <= 0 runs exactly max_iter iterations.
+ */
+static int bicgstabm(const orc_op* op, const cplx* b, int S, const double* sigma, double tol,
+                     int max_iter, int freeze, cplx* x, int* conv_iter, int* iters,
+                     cplx* c_out, cplx* r_out) {
+    long n = op_n(op);
+    if (S <= 0 || max_iter < 0) return ORC_ARG;
+    cplx* r = malloc(sizeof(cplx) * n);
+    cplx* rt = malloc(sizeof(cplx) * n);
+    cplx* p = malloc(sizeof(cplx) * n);
+    cplx* v = malloc(sizeof(cplx) * n);
+    cplx* sv = malloc(sizeof(cplx) * n);
+    cplx* t = malloc(sizeof(cplx) * n);
+    cplx* r_old = malloc(sizeof(cplx) * n);
+    cplx* ps = malloc(sizeof(cplx) * n * S);
+    cplx* zp = malloc(sizeof(cplx) * S);   /* zeta_{k-1} */
+    cplx* z = malloc(sizeof(cplx) * S);    /* zeta_k     */
+    cplx* T = malloc(sizeof(cplx) * S);    /* T_k = prod_{j<k} (1 + sigma omega_j) */
+    int* done = calloc(S, sizeof(int));
+    int status = ORC_OK;
+    memcpy(r, b, sizeof(cplx) * n);
+    memcpy(rt, b, sizeof(cplx) * n);
+    memcpy(p, b, sizeof(cplx) * n);
+    for (int s = 0; s < S; ++s) {
+        memcpy(ps + (long)s * n, b, sizeof(cplx) * n);
+        zp[s] = z[s] = T[s] = 1.0;
+        if (conv_iter) conv_iter[s] = -1;
+    }
+    memset(x, 0, sizeof(cplx) * n * S);
+    cplx rho = dot(n, rt, r);
+    double bnorm = sqrt(norm2(n, b)), rnorm = bnorm;
+    cplx alpha_prev = 1.0, beta_prev = 0.0;
+    int i = 0;
+    if (bnorm == 0.0) {
+        for (int s = 0; s < S; ++s) if (conv_iter) conv_iter[s] = 0;
+        goto out;
+    }
+    while (i < max_iter) {
+        op_apply(op, 0.0, p, v);                              /* v = A p          */
+        cplx rtv = dot(n, rt, v);
+        if (rtv == 0.0 || rho == 0.0) { status = ORC_BREAKDOWN; break; }
+        cplx alpha = rho / rtv;
+        for (long k = 0; k < n; ++k) sv[k] = r[k] - alpha * v[k];
+        op_apply(op, 0.0, sv, t);                             /* t = A s          */
+        double tt = norm2(n, t);
+        if (tt == 0.0) { status = ORC_BREAKDOWN; break; }
+        cplx omega = dot(n, t, sv) / tt;
+        if (omega == 0.0) { status = ORC_BREAKDOWN; break; }
+        /* shifted updates of x and the coefficients (before r changes) */
+        cplx rho_new;
+        memcpy(r_old, r, sizeof(cplx) * n);                        /* r_k     */
+        for (long k = 0; k < n; ++k) r[k] = sv[k] - omega * t[k];   /* r_{k+1} */
+        rho_new = dot(n, rt, r);
+        cplx beta = (rho_new / rho) * (alpha / omega);
+        for (int s = 0; s < S; ++s) {
+            if (freeze && done[s]) continue;
+            cplx zn = z[s] * zp[s] * alpha_prev /
+                      (alpha * beta_prev * (zp[s] - z[s]) + zp[s] * alpha_prev * (1.0 + sigma[s] * alpha));
+            cplx as = alpha * zn / z[s];
+            cplx os = omega / (1.0 + sigma[s] * omega);
+            cplx Tn = T[s] * (1.0 + sigma[s] * omega);
+            cplx cr = z[s] / T[s];      /* r_sigma = cr r_k         */
+            cplx cs = zn / T[s];        /* s_sigma = cs s_k         */
+            cplx crn = zn / Tn;         /* r'_sigma = crn r_{k+1}   */
+            cplx bs = beta * (zn / z[s]) * (zn / z[s]);
+            if (!isfinite(creal(zn)) || !isfinite(cimag(zn)) || Tn == 0.0 || as == 0.0) {
+                status = ORC_BREAKDOWN;
+                break;
+            }
+            cplx* xs = x + (long)s * n;
+            cplx* pss = ps + (long)s * n;
+            for (long k = 0; k < n; ++k) {
+                cplx s_sig = cs * sv[k];
+                cplx r_old_sig = cr * r_old[k];
+                xs[k] += as * pss[k] + os * s_sig;
+                pss[k] = crn * r[k] + bs * (pss[k] - (os / as) * (r_old_sig - s_sig));
+            }
+            zp[s] = z[s];
+            z[s] = zn;
+            T[s] = Tn;
+        }
+        if (status != ORC_OK) break;
+        for (long k = 0; k < n; ++k) p[k] = r[k] + beta * (p[k] - omega * v[k]);
+        rho = rho_new;
+        alpha_prev = alpha;
+        beta_prev = beta;
+        ++i;
+        rnorm = sqrt(norm2(n, r));
+        if (!isfinite(rnorm)) { status = ORC_NONFINITE; break; }
+        int all = 1;
+        for (int s = 0; s < S; ++s) {
+            if (!done[s] && tol > 0 && cabs(z[s] / T[s]) * rnorm <= tol * bnorm) {
+                done[s] = 1;
+                if (conv_iter) conv_iter[s] = i;
+            }
+            all &= done[s];
+        }
+        if (tol > 0 && all) break;
+    }
+    if (status == ORC_OK && tol > 0) {
+        for (int s = 0; s < S; ++s) if (!done[s]) status = ORC_NOT_CONVERGED;
+    }
+out:
+    if (iters) *iters = i;
+    if (c_out) for (int s = 0; s < S; ++s) c_out[s] = z[s] / T[s];
+    if (r_out) memcpy(r_out, r, sizeof(cplx) * n);
+    free(r); free(rt); free(p); free(v); free(sv); free(t); free(r_old); free(ps);
+    free(zp); free(z); free(T); free(done);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
 /* Exported entry points (plain pointers, complex as interleaved pairs) */
 /* ------------------------------------------------------------------ */
 
@@ -412,6 +567,29 @@ int orc_cg_bsr(long nbr, int bd, const int64_t* rp, const int32_t* ci, const dou
                const double* b, double sigma, double tol, int max_iter, double* x, int* iters) {
     orc_op op = bsr_op(nbr, bd, rp, ci, v);
     return cg(&op, (const cplx*)b, sigma, tol, max_iter, (cplx*)x, iters);
+}
+
+int orc_bicgstabm_bsr(long nbr, int bd, const int64_t* rp, const int32_t* ci, const double* v,
+                      const double* b, int S, const double* sigma, double tol, int max_iter,
+                      int freeze, double* x, int* conv_iter, int* iters, double* c_out,
+                      double* r_out) {
+    orc_op op = bsr_op(nbr, bd, rp, ci, v);
+    return bicgstabm(&op, (const cplx*)b, S, sigma, tol, max_iter, freeze, (cplx*)x, conv_iter,
+                     iters, (cplx*)c_out, (cplx*)r_out);
+}
+
+int orc_bicgstabm_dirac(int nc, const int L[4], const double* U, double mass, const double* b,
+                        int S, const double* sigma, double tol, int max_iter, int freeze,
+                        double* x, int* conv_iter, int* iters, double* c_out, double* r_out) {
+    orc_op op = stag_op(nc, L, U, mass);
+    op.kind = 2;
+    return bicgstabm(&op, (const cplx*)b, S, sigma, tol, max_iter, freeze, (cplx*)x, conv_iter,
+                     iters, (cplx*)c_out, (cplx*)r_out);
+}
+
+void orc_dirac_apply_c(int nc, const int L[4], const double* U, double mass, double sigma,
+                       const double* in, double* out) {
+    orc_dirac_apply(nc, L, (const cplx*)U, mass, sigma, (const cplx*)in, (cplx*)out);
 }
 
 void orc_dslash_c(int nc, const int L[4], const double* U, const double* in, double* out) {

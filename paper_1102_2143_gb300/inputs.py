@@ -151,6 +151,68 @@ def poisson_5pt_bsr(N: int):
     return row_ptr, col_idx, v
 
 
+def random_nonhermitian_bsr(nbr: int, bd: int, blocks_per_row: int, shift: float, skew: float, seed: int):
+    """A random non-Hermitian block-CSR matrix: the Hermitian positive-definite
+    B^dagger B + shift*I of random_hpd_bsr plus `skew` times independent
+    complex Gaussian blocks on the same pattern (so the field of values stays
+    in the right half plane for small skew). Returns (row_ptr, col_idx, vals,
+    dense A)."""
+    rp, ci, va, _ = random_hpd_bsr(nbr, bd, blocks_per_row, shift, seed)
+    g = rng(seed + 1)
+    va = va + skew * (g.standard_normal(va.shape) + 1j * g.standard_normal(va.shape)) * math.sqrt(0.5)
+    n = nbr * bd
+    A = np.zeros((n, n), dtype=np.complex128)
+    for i in range(nbr):
+        for k in range(rp[i], rp[i + 1]):
+            j = int(ci[k])
+            A[i * bd:(i + 1) * bd, j * bd:(j + 1) * bd] += va[k]
+    return rp, ci, va, A
+
+
+def staggered_dirac_bsr(links, dims, nc: int, mass: float):
+    """The staggered Dirac operator M = m + D as block-CSR with nc x nc blocks:
+    per site row the diagonal m*I and, per direction mu, the forward hop
+    +1/2 eta_mu(x) U_mu(x) (column x+mu) and the backward hop
+    -1/2 eta_mu(x) U_mu(x-mu)^dagger (column x-mu), columns sorted; hops that
+    land on the same site (extent 2) add. Conventions as in the module
+    docstring. Returns (row_ptr int64, col_idx int32, vals [nnzb][nc][nc])."""
+    dims = tuple(int(d) for d in dims)
+    V = volume(dims)
+    U = np.asarray(links, dtype=np.complex128).reshape(4, V, nc, nc)
+    x = np.arange(V)
+    c = [(x // int(np.prod(dims[:mu]))) % dims[mu] for mu in range(4)]
+    stride = [int(np.prod(dims[:mu])) for mu in range(4)]
+    cols = [x]
+    blks = [np.broadcast_to(mass * np.eye(nc, dtype=np.complex128), (V, nc, nc))]
+    for mu in range(4):
+        par = sum(c[nu] for nu in range(mu)) if mu else np.zeros(V, dtype=np.int64)
+        eta = np.where(par % 2 == 0, 0.5, -0.5)[:, None, None]
+        fwd = np.where(c[mu] == dims[mu] - 1, x - (dims[mu] - 1) * stride[mu], x + stride[mu])
+        bwd = np.where(c[mu] == 0, x + (dims[mu] - 1) * stride[mu], x - stride[mu])
+        cols += [fwd, bwd]
+        blks += [eta * U[mu], -eta * np.conj(np.swapaxes(U[mu][bwd], 1, 2))]
+    cols = np.stack(cols, axis=1)                     # [V][9]
+    blks = np.stack(blks, axis=1)                     # [V][9][nc][nc]
+    order = np.argsort(cols, axis=1, kind="stable")
+    cols = np.take_along_axis(cols, order, axis=1)
+    blks = np.take_along_axis(blks, order[:, :, None, None], axis=1)
+    # merge repeated columns inside a row
+    row_ptr = [0]
+    out_c, out_b = [], []
+    for i in range(V):
+        prev = -1
+        for k in range(9):
+            if cols[i, k] == prev:
+                out_b[-1] = out_b[-1] + blks[i, k]
+            else:
+                out_c.append(cols[i, k])
+                out_b.append(blks[i, k].copy())
+                prev = cols[i, k]
+        row_ptr.append(len(out_c))
+    return (np.asarray(row_ptr, dtype=np.int64), np.asarray(out_c, dtype=np.int32),
+            np.asarray(out_b, dtype=np.complex128))
+
+
 @dataclass
 class PoissonProblem:
     """The shifted family on the 2-D Poisson operator (the paper's test)."""

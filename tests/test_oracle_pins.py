@@ -410,3 +410,82 @@ def test_phi_gradient_closed_form():
             fd = (sp - sm) / (2 * h)
             want = grad[j].real if d == 1.0 else grad[j].imag
             assert abs(fd - want) <= 1e-6 * max(1.0, abs(want))
+
+
+# ----------------------------------------------------------------------------
+# BiCGStab-M: the multi-shift BiCGStab for non-Hermitian families
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bd", [1, 2, 3])
+def test_bicgstabm_matches_dense_solves(bd):
+    rp, ci, va, A = inputs.random_nonhermitian_bsr(24, bd, 4, 0.5, 0.3, 40 + bd)
+    assert np.linalg.norm(A - np.conj(A.T)) > 0.1 * np.linalg.norm(A)   # truly non-Hermitian
+    n = A.shape[0]
+    b = _vec(n, 41)
+    sig = inputs.log_shifts(1e-2, 3.0, 6)
+    res = oracle.bicgstabm_bsr(rp, ci, va, b, sig, 1e-13)
+    assert res.status == 0
+    for s, sv in enumerate(sig):
+        xd = np.linalg.solve(A + sv * np.eye(n), b)
+        assert np.linalg.norm(res.x[s] - xd) <= 1e-10 * np.linalg.norm(xd), (s, sv)
+
+
+def test_bicgstabm_shifted_residuals_are_collinear():
+    """At every iteration b - (A + sigma) x_sigma = (zeta_sigma / T_sigma) r:
+    a dropped term or a wrong factor in any shifted recurrence breaks this."""
+    rp, ci, va, A = inputs.random_nonhermitian_bsr(30, 2, 4, 0.5, 0.3, 51)
+    n = A.shape[0]
+    b = _vec(n, 52)
+    sig = np.array([0.0, 0.02, 0.3, 2.0])
+    for k in (1, 2, 5, 9):
+        res = oracle.bicgstabm_bsr(rp, ci, va, b, sig, 0.0, max_iter=k, freeze=False)
+        assert res.iters == k
+        for s, sv in enumerate(sig):
+            true_r = b - (A @ res.x[s] + sv * res.x[s])
+            assert np.linalg.norm(true_r - res.c[s] * res.r) <= 1e-11 * np.linalg.norm(b), (k, s)
+    # the seed's own first step is the textbook one: x = alpha b + omega s
+    res = oracle.bicgstabm_bsr(rp, ci, va, b, [0.0], 0.0, max_iter=1, freeze=False)
+    v = A @ b
+    alpha = np.vdot(b, b) / np.vdot(b, v)
+    s1 = b - alpha * v
+    t = A @ s1
+    omega = np.vdot(t, s1) / np.vdot(t, t)
+    assert np.linalg.norm(res.x[0] - (alpha * b + omega * s1)) <= 1e-13 * np.linalg.norm(res.x[0])
+
+
+def test_bicgstabm_dirac_family_equals_cgm_on_normal_equations():
+    """(m_s + D) x = b has x = (m_s - D) y with y = (m_s^2 - D^2)^{-1} b, the
+    CG-M family of A = m^2 - D^2 at shifts m_s^2 - m^2: two different
+    algorithms on two different operators must agree."""
+    dims, nc, m = (4, 4, 4, 6), 3, 0.1
+    U = inputs.su_n_links(dims, nc, 0.6, 61)
+    n = inputs.volume(dims) * nc
+    b = _vec(n, 62)
+    sig = inputs.log_shifts(1e-3, 1.0, 5)
+    res = oracle.bicgstabm_dirac(U, dims, nc, m, b, sig, 1e-13)
+    assert res.status == 0
+    ms = m + sig
+    y = oracle.cgm_staggered(U, dims, nc, m, b, ms ** 2 - m ** 2, 1e-13)
+    assert y.status == 0
+    for s in range(len(sig)):
+        want = ms[s] * y.x[s] - oracle.dslash(U, dims, nc, y.x[s])
+        assert np.linalg.norm(res.x[s] - want) <= 1e-9 * np.linalg.norm(want), s
+        r = b - oracle.dirac_apply(U, dims, nc, m, res.x[s], sigma=sig[s])
+        assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_staggered_dirac_bsr_matches_oracle_operator():
+    dims, nc, m = (4, 2, 4, 6), 2, 0.3
+    U = inputs.su_n_links(dims, nc, 0.7, 71)
+    rp, ci, va = inputs.staggered_dirac_bsr(U, dims, nc, m)
+    n = inputs.volume(dims) * nc
+    v = _vec(n, 72)
+    got = oracle.bsr_apply(rp, ci, va, v, sigma=0.25)
+    want = oracle.dirac_apply(U, dims, nc, m, v, sigma=0.25)
+    assert np.linalg.norm(got - want) <= 1e-14 * np.linalg.norm(want)
+
+
+def test_bicgstabm_zero_source():
+    rp, ci, va, A = inputs.random_nonhermitian_bsr(10, 3, 3, 0.5, 0.3, 81)
+    res = oracle.bicgstabm_bsr(rp, ci, va, np.zeros(30, np.complex128), [0.1, 1.0], 1e-10)
+    assert res.status == 0 and res.iters == 0 and np.all(res.x == 0)
