@@ -51,6 +51,7 @@ extern "C" {
 #define MSC_ERR_NOT_CONVERGED 6  /* iteration cap reached; x is written, see info */
 #define MSC_ERR_TIMEOUT       7  /* reserved: a bounded device wait gave up */
 #define MSC_ERR_UNSUPPORTED   8  /* valid request this build does not handle */
+#define MSC_ERR_BREAKDOWN     9  /* msc_solve_nonherm: a BiCGStab denominator vanished */
 
 /* precision of the iteration */
 #define MSC_FP64  0  /* every vector, link, block and scalar in FP64 */
@@ -208,6 +209,27 @@ typedef struct {
 int msc_solve(msc_ctx* ctx, const msc_op* op, const double* b, int nrhs,
               const double* sigma, int S, const msc_params* params, double* x,
               msc_info* info);
+
+/* Non-Hermitian shifted families: (A + sigma_s I) x_{r,s} = b_r for every
+ * shift by multi-shift BiCGStab (BiCGStab-M), the solver the paper names for
+ * non-Hermitian operators (Sec. 1, Sec. 3; the recurrences are not printed
+ * there). One BiCGStab sequence on A + sigma_0 (sigma_0 = the smallest shift,
+ * shadow residual b) serves every shift: the BiCG part of each shifted
+ * residual follows CG-M's zeta recurrence and the stabilising step becomes
+ * omega_s = omega / (1 + (sigma_s - sigma_0) omega), so no shifted system
+ * applies A (two operator applications per iteration in all).
+ * op: a block-CSR operator from msc_op_bsr (any matrix; Hermiticity is not
+ * required); a staggered operator gives MSC_ERR_UNSUPPORTED (the staggered
+ * Dirac matrix m + D enters as block-CSR). params: tol, max_iter and
+ * freeze_converged are used; precision must be MSC_FP64 (else
+ * MSC_ERR_UNSUPPORTED). sigma: [S] host array, any finite values. b, x, info
+ * as in msc_solve; info->true_rel_resid holds the FP64 true residual of
+ * every x_s, computed after the iteration, and a shift above tol gives
+ * MSC_ERR_NOT_CONVERGED. A vanishing denominator gives MSC_ERR_BREAKDOWN (x
+ * is then left as it was at the breakdown). */
+int msc_solve_nonherm(msc_ctx* ctx, const msc_op* op, const double* b, int nrhs,
+                      const double* sigma, int S, const msc_params* params, double* x,
+                      msc_info* info);
 
 /* Rational pseudofermion action and its adjoint (the quadratic form that the
  * shifted family diagonalises, Sec. 1-2; sigma_s and c_s come from a rational

@@ -31,6 +31,7 @@ MSC_ERR_NONFINITE = 5
 MSC_ERR_NOT_CONVERGED = 6
 MSC_ERR_TIMEOUT = 7
 MSC_ERR_UNSUPPORTED = 8
+MSC_ERR_BREAKDOWN = 9
 
 MSC_FP64 = 0
 MSC_MIXED = 1
@@ -97,6 +98,8 @@ SIGNATURES = {
     "msc_op_apply_noalloc": (_I, [_VP, _D, _VP, _VP, _VP]),
     "msc_params_default": (None, [ctypes.POINTER(msc_params)]),
     "msc_solve": (_I, [_VP, _VP, _VP, _I, _VP, _I, ctypes.POINTER(msc_params), _VP,
+                       ctypes.POINTER(msc_info)]),
+    "msc_solve_nonherm": (_I, [_VP, _VP, _VP, _I, _VP, _I, ctypes.POINTER(msc_params), _VP,
                        ctypes.POINTER(msc_info)]),
     "msc_strerror": (ctypes.c_char_p, [_I]),
     "msc_quad_form": (_I, [_VP, _VP, _VP, _I, _VP, _VP, ctypes.POINTER(_D)]),
@@ -281,6 +284,14 @@ def msc_solve(ctx: int, op: int, b, nrhs: int, sigma, S: int, params: msc_params
                             ctypes.byref(info) if info is not None else None)
 
 
+def msc_solve_nonherm(ctx: int, op: int, b, nrhs: int, sigma, S: int, params: msc_params, x,
+                      info: msc_info | None = None) -> int:
+    """Raw call of the BiCGStab-M solve; returns the status."""
+    return load().msc_solve_nonherm(ctx, op, _ptr(b), int(nrhs), _ptr(sigma), int(S),
+                                    ctypes.byref(params), _ptr(x),
+                                    ctypes.byref(info) if info is not None else None)
+
+
 # ---------------------------------------------------------------------------
 # convenience layer (still only marshalling)
 # ---------------------------------------------------------------------------
@@ -333,6 +344,50 @@ def solve(ctx: int, op: int, b, sigma, x=None, tol=1e-10, precision=MSC_MIXED, m
     st = msc_solve(ctx, op, b, nrhs, sig, S, p, x, info)
     if st != MSC_OK and (raise_on_error and st != MSC_ERR_NOT_CONVERGED):
         raise MscError(st, "msc_solve")
+    res = SolveInfo(info, it.reshape(nrhs, S), rit.reshape(nrhs, S), rho.reshape(nrhs, S))
+    if squeeze:
+        x = x[0]
+    return x, res
+
+
+def solve_nonherm(ctx: int, op: int, b, sigma, x=None, tol=1e-10, max_iter=100000, freeze=True,
+                  raise_on_error=True):
+    """Non-Hermitian shifted family by BiCGStab-M (FP64, block-CSR operator).
+    `b`: [nrhs][n] (or [n]) complex128, numpy or torch, host or device; `x`
+    (optional) receives [nrhs][S][n]. Returns (x, SolveInfo)."""
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    S = int(sig.shape[0])
+    squeeze = False
+    if hasattr(b, "data_ptr"):
+        import torch
+        if b.dim() == 1:
+            b = b.unsqueeze(0)
+            squeeze = True
+        b = b.contiguous()
+        nrhs, n = b.shape
+        if x is None:
+            x = torch.empty((nrhs, S, n), dtype=torch.complex128, device=b.device)
+    else:
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        if b.ndim == 1:
+            b = b[None, :]
+            squeeze = True
+        nrhs, n = b.shape
+        if x is None:
+            x = np.empty((nrhs, S, n), dtype=np.complex128)
+    p = msc_params_default()
+    p.tol, p.max_iter, p.precision = float(tol), int(max_iter), MSC_FP64
+    p.freeze_converged = int(bool(freeze))
+    it = np.zeros(nrhs * S, dtype=np.int32)
+    rit = np.zeros(nrhs * S, dtype=np.int32)
+    rho = np.zeros(nrhs * S, dtype=np.float64)
+    info = msc_info()
+    info.shift_iters = it.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    info.shift_refine_iters = rit.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    info.true_rel_resid = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = msc_solve_nonherm(ctx, op, b, nrhs, sig, S, p, x, info)
+    if st != MSC_OK and (raise_on_error and st != MSC_ERR_NOT_CONVERGED):
+        raise MscError(st, "msc_solve_nonherm")
     res = SolveInfo(info, it.reshape(nrhs, S), rit.reshape(nrhs, S), rho.reshape(nrhs, S))
     if squeeze:
         x = x[0]

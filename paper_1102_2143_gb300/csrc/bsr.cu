@@ -9,11 +9,9 @@
 // blocks pointing at column 0.
 #include <algorithm>
 
-#include "engine.h"
+#include "bsr.cuh"
 
 namespace msc {
-
-template <class T> using T2 = typename C2<T>::t;
 
 __global__ void k_bsr_pack(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                            const double2* __restrict__ vals, int64_t nbr, int bd,
@@ -57,34 +55,6 @@ cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
     k_bsr_pack<<<(int)b, 256, 0, st>>>(d_row_ptr, d_col, d_vals, op.nbr, op.bd, op.slice_len,
                                         op.slice_start, op.cols, op.vals64, op.vals32, d_bad);
     return cudaGetLastError();
-}
-
-// y = A src for one row (thread = row, lanes of a warp = rows of a slice).
-// Slice bases are 64-bit; offsets inside a slice (k * 32 * BD * BD) stay
-// 32-bit; the source gathers go through the read-only path.
-template <class T, int BD>
-__device__ __forceinline__ void bsr_row(const OpDev& A, const T2<T>* __restrict__ vals,
-                                        const T2<T>* __restrict__ src, int row, T2<T> (&y)[BD]) {
-    const int slice = row >> 5;
-    const int lane = row & 31;
-    const int len = __ldg(&A.slice_len[slice]);
-    const int64_t st = __ldg(&A.slice_start[slice]);
-#pragma unroll
-    for (int a = 0; a < BD; ++a) y[a] = {T(0), T(0)};
-    const int32_t* __restrict__ cp = A.cols + st * 32 + lane;
-    const T2<T>* __restrict__ vp = vals + st * BD * BD * 32 + lane;
-#pragma unroll 3
-    for (int k = 0; k < len; ++k) {
-        const int c = __ldg(cp + k * 32);
-        T2<T> xv[BD];
-#pragma unroll
-        for (int b = 0; b < BD; ++b) xv[b] = __ldg(src + (size_t)c * BD + b);
-        const T2<T>* vk = vp + k * (BD * BD * 32);
-#pragma unroll
-        for (int a = 0; a < BD; ++a)
-#pragma unroll
-            for (int b = 0; b < BD; ++b) cfma(y[a], __ldg(vk + (a * BD + b) * 32), xv[b]);
-    }
 }
 
 // FP32: four 256-thread blocks per SM at up to 64 registers (at five blocks

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/msc.h"
+#include "bicgstab.cuh"
 #include "engine.h"
 
 using namespace msc;
@@ -59,6 +60,7 @@ struct msc_ctx {
     Buf coef, force;  // adjoint: weights c_s and a link-shaped output
     Buf btab;         // batched solves: system table, operator table, block maps
     Buf actb;         // {count, indices} of the systems still iterating (refinement)
+    Buf bcg;          // BiCGStab-M scalars: one BcgSys, then S BcgSlot
     Buf condf;        // one flag per iteration of a chunk graph (conditional update bodies)
     int use_cond = 1; // build reliable updates as conditional graph nodes
     int* h_flags = nullptr;  // pinned copy of the conditional flags of a chunk
@@ -552,6 +554,7 @@ const char* msc_strerror(int code) {
         case MSC_ERR_NOT_CONVERGED: return "iteration cap reached before tolerance";
         case MSC_ERR_TIMEOUT: return "bounded device wait gave up";
         case MSC_ERR_UNSUPPORTED: return "unsupported request";
+        case MSC_ERR_BREAKDOWN: return "BiCGStab-M breakdown (a recurrence denominator vanished)";
         default: return "unknown status";
     }
 }
@@ -607,7 +610,7 @@ int msc_destroy(msc_ctx* c) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     Buf* bufs[] = {&c->sys, &c->slot, &c->partial, &c->counter, &c->out_red, &c->descs,
                    &c->b64, &c->x64, &c->t64, &c->r, &c->p, &c->t, &c->ps, &c->xit,
-                   &c->coef, &c->force, &c->btab, &c->actb, &c->condf};
+                   &c->coef, &c->force, &c->btab, &c->actb, &c->condf, &c->bcg};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_sys) cudaFreeHost(c->h_sys);
@@ -1124,6 +1127,155 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         info->rupdate_ms = pa.n ? pa.k2 / pa.n : 0.0;
         info->update_ms = pa.n ? pa.k3 / pa.n : 0.0;
         info->prof_samples = pa.n;
+    }
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// Non-Hermitian families: multi-shift BiCGStab (BiCGStab-M), FP64
+// ---------------------------------------------------------------------------
+
+int msc_solve_nonherm(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const double* sigma, int S,
+                      const msc_params* prm_in, double* x, msc_info* info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || !op || !b || !x || !sigma || nrhs <= 0 || S <= 0 || S > kMaxShifts) return MSC_ERR_ARG;
+    msc_params prm;
+    msc_params_default(&prm);
+    if (prm_in) prm = *prm_in;
+    if (!(prm.tol > 0) || prm.max_iter < 0) return MSC_ERR_ARG;
+    for (int s = 0; s < S; ++s)
+        if (!std::isfinite(sigma[s])) return MSC_ERR_ARG;
+    if (op->dev.kind != OP_BSR || prm.precision != MSC_FP64) return MSC_ERR_UNSUPPORTED;
+    int st = begin(c);
+    if (st) return st;
+    const OpDev& A = op->dev;
+    const int64_t n = A.n, npad = (n + 63) / 64 * 64;
+    st = ensure_ws(c, npad, std::max(6, S), S, 1, 16);
+    if (st) return st;
+    {
+        bool moved = false;
+        CK(grow(c, c->bcg, sizeof(BcgSys) + sizeof(BcgSlot) * S, moved));
+        if (moved) c->gen++;
+    }
+    const long launches0 = c->launches;
+    BcgSys* dsys = (BcgSys*)c->bcg.p;
+    BcgSlot* dslot = (BcgSlot*)((char*)c->bcg.p + sizeof(BcgSys));
+    double2* b64 = (double2*)c->b64.p;
+    BcgVec v;
+    v.r[0] = (double2*)c->r.p;
+    v.r[1] = (double2*)c->r.p + npad;
+    v.rt = b64;
+    v.p = (double2*)c->p.p;
+    v.v = (double2*)c->t.p;
+    v.s = (double2*)c->t.p + npad;
+    v.t = (double2*)c->t.p + 2 * npad;
+    v.x = (double2*)c->x64.p;
+    v.ps = (double2*)c->ps.p;
+    v.n = n;
+    v.npad = npad;
+    int base = 0;
+    for (int s = 1; s < S; ++s)
+        if (sigma[s] < sigma[base]) base = s;
+    Engine e = engine_of(c);
+    // a chunk of 16 iterations (even, so the residual buffers return to
+    // their roles) as one CUDA graph
+    const int chunk = 16;
+    char key[128];
+    snprintf(key, sizeof key, "bcg|%ld|%d|%lld", op->uid, S, (long long)npad);
+    GraphEntry& ge = c->graphs[key];
+    if (!ge.exec || ge.gen != c->gen) {
+        if (ge.exec) cudaGraphExecDestroy(ge.exec);
+        ge.exec = nullptr;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
+        cudaError_t err = cudaSuccess;
+        for (int it = 0; it < chunk && err == cudaSuccess; ++it)
+            err = launch_bcg_iter(A, e, dsys, dslot, v, S, it & 1, c->work);
+        cudaError_t err2 = cudaStreamEndCapture(c->work, &g);
+        if (err != cudaSuccess || err2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_status(err != cudaSuccess ? err : err2);
+        }
+        err = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (err != cudaSuccess) return cuda_status(err);
+        ge.gen = c->gen;
+        ge.kernels = 5 * chunk;
+    }
+    std::vector<BcgSlot> hslot(S);
+    std::vector<int> shift_iters((size_t)nrhs * S, -1);
+    std::vector<double> rho((size_t)nrhs * S, std::nan(""));
+    int status = MSC_OK, iters = 0;
+    for (int j = 0; j < nrhs && status == MSC_OK; ++j) {
+        CK(cudaMemcpyAsync(b64, b + (size_t)j * n * 2, n * 16, cudaMemcpyDefault, c->work));
+        BcgSys hs;
+        memset(&hs, 0, sizeof hs);
+        hs.alpha_prev = {1.0, 0.0};
+        hs.tol2 = prm.tol * prm.tol;
+        hs.sigma0 = sigma[base];
+        hs.status = ST_RUNNING;
+        hs.max_iter = prm.max_iter;
+        hs.S = S;
+        hs.base = base;
+        hs.freeze = prm.freeze_converged;
+        for (int s = 0; s < S; ++s) {
+            BcgSlot& q = hslot[s];
+            memset(&q, 0, sizeof q);
+            q.sigma_rel = sigma[s] - sigma[base];
+            q.zeta = q.zeta_prev = q.zeta_new = q.T = q.T_new = {1.0, 0.0};
+            q.active = 1;
+            q.conv_iter = -1;
+        }
+        CK(cudaMemcpyAsync(dsys, &hs, sizeof hs, cudaMemcpyHostToDevice, c->work));
+        CK(cudaMemcpyAsync(dslot, hslot.data(), sizeof(BcgSlot) * S, cudaMemcpyHostToDevice, c->work));
+        CK(launch_bcg_init(e, dsys, dslot, v, S, c->work));
+        c->launches++;
+        CK(cudaMemcpyAsync(&hs, dsys, sizeof hs, cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        const long max_chunks = (long)prm.max_iter / chunk + 2;
+        for (long k = 0; k < max_chunks && hs.status == ST_RUNNING; ++k) {
+            CK(cudaGraphLaunch(ge.exec, c->work));
+            c->launches += ge.kernels;
+            CK(cudaMemcpyAsync(&hs, dsys, sizeof hs, cudaMemcpyDeviceToHost, c->work));
+            CK(cudaStreamSynchronize(c->work));
+        }
+        CK(cudaMemcpyAsync(hslot.data(), dslot, sizeof(BcgSlot) * S, cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+        iters = std::max(iters, hs.it);
+        for (int s = 0; s < S; ++s) shift_iters[(size_t)j * S + s] = hslot[s].conv_iter;
+        if (hs.status == ST_ERR_BREAKDOWN) status = MSC_ERR_BREAKDOWN;
+        else if (hs.status == ST_ERR_NONFINITE) status = MSC_ERR_NONFINITE;
+        // FP64 true residual of every shift: |b - (A + sigma_s) x_s|^2 into out_red[s]
+        for (int s = 0; s < S; ++s)
+            hsec(c, D_RIC)[s] = mkdesc(v.x + (size_t)s * npad, v.x + (size_t)s * npad, b64, nullptr, sigma[s], -1,
+                                       s, FIN_STORE);
+        CK(upload_sec(c, D_RIC, S));
+        CK(op_pass(c, A, PREC_F64, PASS_C, 0, D_RIC, S, nullptr, nullptr, true));
+        CK(cudaMemcpyAsync(c->h_red, c->out_red.p, sizeof(double) * S, cudaMemcpyDeviceToHost, c->work));
+        CK(cudaMemcpy2DAsync(x + (size_t)j * S * n * 2, n * 16, v.x, npad * 16, n * 16, S, cudaMemcpyDefault,
+                             c->work));
+        CK(cudaStreamSynchronize(c->work));
+        for (int s = 0; s < S; ++s)
+            rho[(size_t)j * S + s] = hs.bnorm2 > 0 ? std::sqrt(c->h_red[s] / hs.bnorm2) : 0.0;
+        if (status == MSC_OK) {
+            for (int s = 0; s < S; ++s)
+                if (!(rho[(size_t)j * S + s] <= prm.tol)) status = MSC_ERR_NOT_CONVERGED;
+        }
+    }
+    if (info) {
+        info->status = status;
+        info->iters = iters;
+        info->refine_rounds = info->refine_iters = 0;
+        info->reliable_updates = info->refine_reliable_updates = 0;
+        info->kernel_launches = (int)(c->launches - launches0);
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (size_t g = 0; g < (size_t)nrhs * S; ++g) {
+            if (info->shift_iters) info->shift_iters[g] = shift_iters[g];
+            if (info->shift_refine_iters) info->shift_refine_iters[g] = 0;
+            if (info->true_rel_resid) info->true_rel_resid[g] = rho[g];
+        }
+        info->op_ms = info->rupdate_ms = info->update_ms = 0.0;
+        info->prof_samples = 0;
     }
     return status;
 }

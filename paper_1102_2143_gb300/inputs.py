@@ -196,6 +196,9 @@ def staggered_dirac_bsr(links, dims, nc: int, mass: float):
     order = np.argsort(cols, axis=1, kind="stable")
     cols = np.take_along_axis(cols, order, axis=1)
     blks = np.take_along_axis(blks, order[:, :, None, None], axis=1)
+    if min(dims) > 2:       # no two hops of a row land on the same site
+        return (np.arange(V + 1, dtype=np.int64) * 9, cols.reshape(-1).astype(np.int32),
+                np.ascontiguousarray(blks.reshape(-1, nc, nc)))
     # merge repeated columns inside a row
     row_ptr = [0]
     out_c, out_b = [], []
