@@ -40,15 +40,24 @@ L2_BYTES = 129 * 2 ** 20
 
 
 SPMV_COUNTERS = os.path.join(ROOT, "profiles", "bsr_spmv_24x4_counters.md")
-SPMV_SOURCES = ("common.cuh", "engine.h", "bsr.cu")
+# the profiled kernel: its own text in bsr.cu (from its leading comment to
+# the next launcher template) and the two headers it depends on
+SPMV_HEADERS = ("common.cuh", "engine.h")
+SPMV_KERNEL = ("bsr.cu", "// The FP32 PASS_A of a single system",
+               "template <class T, int BD, int KIND, class TO>\nstatic void launch_one(")
 
 
 def spmv_source_hash():
     import hashlib
+    csrc = os.path.join(ROOT, "paper_1102_2143_gb300", "csrc")
     h = hashlib.sha256()
-    for name in SPMV_SOURCES:
-        with open(os.path.join(ROOT, "paper_1102_2143_gb300", "csrc", name), "rb") as f:
+    for name in SPMV_HEADERS:
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
+    with open(os.path.join(csrc, SPMV_KERNEL[0])) as f:
+        src = f.read()
+    a = src.index(SPMV_KERNEL[1])
+    h.update(src[a:src.index(SPMV_KERNEL[2], a)].encode())
     return h.hexdigest()
 
 
