@@ -281,6 +281,35 @@ def test_argument_and_breakdown_errors(ctx):
     msc.msc_op_destroy(bop)
 
 
+def test_maximum_shift_count_and_size_limits(ctx):
+    """128 shifts (the most a system takes) in FP64 and mixed precision, each
+    x_s against the oracle; 129 shifts, an empty operator and a block row
+    longer than the kernels' 32-bit in-slice offsets allow are rejected."""
+    p = inputs.lattice_4x4_su3_8shifts()
+    op = stag_op(ctx, p.links, p.dims, p.nc, p.mass)
+    sig = inputs.log_shifts(1e-3, 10.0, 128)
+    ref = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, p.b[0], sig, 1e-13)
+    assert ref.status == 0
+    for prec in (msc.MSC_FP64, msc.MSC_MIXED):
+        x, info = msc.solve(ctx, op, p.b[0], sig, precision=prec)
+        rho = oracle.true_residual_staggered(p.links, p.dims, p.nc, p.mass, p.b[0], sig, x)
+        check_solution(x, ref.x, rho)
+    with pytest.raises(msc.MscError) as e:
+        msc.solve(ctx, op, p.b[0], inputs.log_shifts(1e-3, 10.0, 129))
+    assert e.value.code == msc.MSC_ERR_ARG
+    msc.msc_op_destroy(op)
+    with pytest.raises(msc.MscError) as e:
+        msc.msc_op_bsr(ctx, 0, 1, np.zeros(1, np.int64), np.zeros(0, np.int32),
+                       np.zeros((0, 1, 1), np.complex128))
+    assert e.value.code == msc.MSC_ERR_ARG
+    # one block row of 2^26 / 9 + 1 blocks of 3 x 3: beyond the limit
+    m = (1 << 26) // 9 + 1
+    with pytest.raises(msc.MscError) as e:
+        msc.msc_op_bsr(ctx, 1, 3, np.array([0, m], np.int64), np.zeros(m, np.int32),
+                       np.zeros((m, 3, 3), np.complex128))
+    assert e.value.code == msc.MSC_ERR_ARG
+
+
 def test_no_freeze_matches_freeze(ctx):
     p = inputs.lattice_4x4_su3_8shifts()
     op = stag_op(ctx, p.links, p.dims, p.nc, p.mass)
