@@ -125,6 +125,8 @@ int msc_op_apply(msc_ctx* ctx, const msc_op* op, double sigma, const double* in,
 /* out = D in for a staggered operator (FP64). */
 int msc_op_dslash(msc_ctx* ctx, const msc_op* op, const double* in, double* out);
 
+/* Free an operator and the solve graphs its context cached for it. Waits for
+ * the context's queued work; the context must still exist. */
 int msc_op_destroy(msc_op* op);
 
 /* out = (A + sigma) in for a staggered operator, in FP64, without allocating

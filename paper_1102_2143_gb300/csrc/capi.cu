@@ -636,7 +636,21 @@ static void free_op_dev(OpDev& d) {
 
 int msc_op_destroy(msc_op* op) {
     if (!op) return MSC_ERR_ARG;
-    if (op->ctx) cudaSetDevice(op->ctx->device);
+    if (msc_ctx* c = op->ctx) {
+        cudaSetDevice(c->device);
+        // the context's graphs of this operator ("<uid>|..." and "bcg|<uid>|...")
+        // go with it, after the work stream has drained
+        if (c->work) cudaStreamSynchronize(c->work);
+        const std::string a = std::to_string(op->uid) + "|", b = "bcg|" + a;
+        for (auto it = c->graphs.begin(); it != c->graphs.end();) {
+            if (it->first.compare(0, a.size(), a) == 0 || it->first.compare(0, b.size(), b) == 0) {
+                if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+                it = c->graphs.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
     free_op_dev(op->dev);
     delete op;
     return MSC_OK;
