@@ -129,7 +129,7 @@ k_bsr(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A, const
 // `act` (optional): the passes still to run, act[0] = their count and
 // act[1..] their indices, so that groups stay full as systems finish.
 template <class T, int BD, int G>
-__global__ void __launch_bounds__(kThreads, G >= 8 ? 2 : (G >= 4 ? 3 : (G >= 3 ? 4 : 5)))
+__global__ void __launch_bounds__(kThreads, 5)
 k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int groups, OpDev A,
             const T2<T>* __restrict__ vals) {
     __shared__ PassDesc sd[G];
@@ -307,12 +307,8 @@ static void launch_multi_g(const Engine& e, const PassDesc* descs, int npass, co
 template <int BD>
 static void launch_multi(const Engine& e, const PassDesc* descs, int npass, const int* act, int group,
                          int groups, const OpDev& A, cudaStream_t st) {
-    switch (group) {
-        case 1: launch_multi_g<BD, 1>(e, descs, npass, act, groups, A, st); break;
-        case 2: launch_multi_g<BD, 2>(e, descs, npass, act, groups, A, st); break;
-        case 4: launch_multi_g<BD, 4>(e, descs, npass, act, groups, A, st); break;
-        default: launch_multi_g<BD, 8>(e, descs, npass, act, groups, A, st); break;
-    }
+    if (group == 1) launch_multi_g<BD, 1>(e, descs, npass, act, groups, A, st);
+    else launch_multi_g<BD, 2>(e, descs, npass, act, groups, A, st);
 }
 
 cudaError_t launch_bsr_multi(const OpDev& op, const Engine& e, const PassDesc* d_descs, int npass,

@@ -57,7 +57,7 @@ cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, c
 cudaError_t launch_bsr_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
                             const PassDesc* d_descs, int npass, cudaStream_t st, const int* act = nullptr,
                             bool per_system = false, const PassDesc* h_desc = nullptr);
-// FP32 SpMV of several systems sharing the matrix, `group` (1, 2, 4, 8)
+// FP32 SpMV of several systems sharing the matrix, `group` (1 or 2)
 // systems per block row of the grid, `groups` rows; `act` (device, optional)
 // = {count, indices...} of the systems to run, read when the kernel runs.
 // kMultiGroup: the group size the solver uses for two or more systems.

@@ -100,3 +100,28 @@ def test_nonherm_edges(ctx):
     assert e.value.code == msc.MSC_ERR_ARG
     msc.msc_op_destroy(sop)
     msc.msc_op_destroy(op)
+
+
+def test_breakdown_is_reported(ctx):
+    """A real skew-symmetric A and a real b: b^T A b = 0, so the first
+    denominator (r~, A p) of BiCGStab vanishes; the solve reports it."""
+    nbr = 16
+    rp, ci, va = [0], [], []
+    for i in range(nbr):
+        if i > 0:
+            ci.append(i - 1); va.append(-1.0)
+        if i < nbr - 1:
+            ci.append(i + 1); va.append(1.0)
+        rp.append(len(ci))
+    rp, ci = np.asarray(rp, np.int64), np.asarray(ci, np.int32)
+    va = np.asarray(va, np.complex128).reshape(-1, 1, 1)
+    b = np.arange(1, nbr + 1, dtype=np.float64).astype(np.complex128)
+    assert oracle.bicgstabm_bsr(rp, ci, va, b, [0.0], 1e-10).status == 7
+    op = msc.msc_op_bsr(ctx, nbr, 1, rp, ci, va)
+    with pytest.raises(msc.MscError) as e:
+        msc.solve_nonherm(ctx, op, b, [0.0])
+    assert e.value.code == msc.MSC_ERR_BREAKDOWN
+    # the context stays usable
+    x, info = msc.solve_nonherm(ctx, op, b, [2.0])
+    assert info.status == 0
+    msc.msc_op_destroy(op)

@@ -489,3 +489,24 @@ def test_bicgstabm_zero_source():
     rp, ci, va, A = inputs.random_nonhermitian_bsr(10, 3, 3, 0.5, 0.3, 81)
     res = oracle.bicgstabm_bsr(rp, ci, va, np.zeros(30, np.complex128), [0.1, 1.0], 1e-10)
     assert res.status == 0 and res.iters == 0 and np.all(res.x == 0)
+
+
+def _skew_bsr(nbr):
+    """A real skew-symmetric tridiagonal matrix as 1x1 block-CSR: for any real
+    b, b^T A b = 0, so BiCGStab's first (r~, A p) = b^T A b vanishes."""
+    rp, ci, va = [0], [], []
+    for i in range(nbr):
+        if i > 0:
+            ci.append(i - 1); va.append(-1.0)
+        if i < nbr - 1:
+            ci.append(i + 1); va.append(1.0)
+        rp.append(len(ci))
+    return (np.asarray(rp, np.int64), np.asarray(ci, np.int32),
+            np.asarray(va, np.complex128).reshape(-1, 1, 1))
+
+
+def test_bicgstabm_breakdown_is_reported():
+    rp, ci, va = _skew_bsr(16)
+    b = np.arange(1, 17, dtype=np.float64).astype(np.complex128)
+    res = oracle.bicgstabm_bsr(rp, ci, va, b, [0.0], 1e-10)
+    assert res.status == 7      # breakdown
