@@ -166,8 +166,9 @@ typedef struct {
     double reliable_delta;/* MSC_MIXED: FP64 reliable update as soon as the iterated
                             residual norm falls below reliable_delta times its
                             largest value since the last update (0 <= delta < 1;
-                            0: only the iteration count triggers it). Keeps the
-                            FP32 drift small next to the residual it corrupts. */
+                            0: only the iteration count triggers it; a tenth of
+                            it in the refinement of a shift). Keeps the FP32
+                            drift small next to the residual it corrupts. */
 } msc_params;
 
 /* Fill defaults: tol 1e-10, max_iter 100000, MSC_MIXED, reliable_every 50,

@@ -1049,12 +1049,16 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
                 const double dk = dstag + sigma[s];
                 init_sys(c->h_sys[k], 1, 0, g, rhs, dk, 0.5 * prm.tol, prm.max_iter, 1, prm);
                 c->h_sys[k].tol2_acc = prm.tol * prm.tol;
-                // a refinement starts from an FP64 residual and needs few
-                // reliable updates beyond the ones its residual's fall
-                // triggers: the iteration cap between updates is 4x the
-                // multi-shift stage's (24^4 block-CSR solve: 24 instead of
-                // 33 FP64 residuals, same iterations and final residuals)
+                // a refinement starts from a small FP64 residual, so its
+                // FP32 drift (about 6e-8 times the largest residual since the
+                // last update) stays far below tol for longer: the iteration
+                // cap between updates is 4x the multi-shift stage's and the
+                // residual-fall trigger is delta/10 (24^4 block-CSR solve: 13
+                // instead of 33 FP64 residuals, 255 -> 247 ms, same iterations
+                // and final residuals; without the fall trigger the FP32
+                // iteration drifts off and ends non-finite)
                 c->h_sys[k].ru_every = 4 * prm.reliable_every;
+                c->h_sys[k].delta2 = 0.01 * prm.reliable_delta * prm.reliable_delta;
                 c->h_sys[k].bnorm2 = bnorm2[rhs];
                 init_slot(c->h_slot[g], 0.0);
                 const double2* bj = b64 + (size_t)rhs * npad;
