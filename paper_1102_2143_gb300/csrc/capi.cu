@@ -466,7 +466,8 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
     }
     CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost, c->work));
     CK(cudaStreamSynchronize(c->work));
-    const long max_chunks = (long)max_iter / chunk + 2;
+    // max_iter = 0 runs no iteration (the device sees the cap only after one)
+    const long max_chunks = max_iter > 0 ? (long)max_iter / chunk + 2 : 0;
     for (long k = 0; k < max_chunks; ++k) {
         bool any = false, all_running = true;
         int active = 0;
@@ -1250,7 +1251,8 @@ int msc_solve_nonherm(msc_ctx* c, const msc_op* op, const double* b, int nrhs, c
         c->launches++;
         CK(cudaMemcpyAsync(&hs, dsys, sizeof hs, cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
-        const long max_chunks = (long)prm.max_iter / chunk + 2;
+        // max_iter = 0 runs no iteration (the cap is seen only after one)
+        const long max_chunks = prm.max_iter > 0 ? (long)prm.max_iter / chunk + 2 : 0;
         for (long k = 0; k < max_chunks && hs.status == ST_RUNNING; ++k) {
             CK(cudaGraphLaunch(ge.exec, c->work));
             c->launches += ge.kernels;
@@ -1570,7 +1572,8 @@ static int run_stage_b(msc_ctx* c, int prec, int J, int chunk, bool reliable, co
     if (st) return st;
     CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * J, cudaMemcpyDeviceToHost, c->work));
     CK(cudaStreamSynchronize(c->work));
-    const long max_chunks = (long)max_iter / chunk + 2;
+    // max_iter = 0 runs no iteration (the device sees the cap only after one)
+    const long max_chunks = max_iter > 0 ? (long)max_iter / chunk + 2 : 0;
     std::vector<int> list;
     list.reserve(J);
     for (long k = 0; k < max_chunks; ++k) {

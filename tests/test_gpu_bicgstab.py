@@ -89,6 +89,8 @@ def test_nonherm_edges(ctx):
     assert np.linalg.norm(b - (A @ x[0] + 0.25 * x[0])) <= 1e-10 * np.linalg.norm(b)
     x, info = msc.solve_nonherm(ctx, op, b, [0.0, 1.0], max_iter=2, raise_on_error=False)
     assert info.status == msc.MSC_ERR_NOT_CONVERGED and info.iters == 2
+    x, info = msc.solve_nonherm(ctx, op, b, [0.5], max_iter=0, raise_on_error=False)
+    assert info.status == msc.MSC_ERR_NOT_CONVERGED and info.iters == 0 and np.all(x == 0)
     # what the solver does not take
     p = inputs.lattice_4x4_su3_8shifts()
     sop = msc.msc_op_staggered(ctx, p.nc, p.dims, p.links, p.mass)

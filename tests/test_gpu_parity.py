@@ -270,6 +270,9 @@ def test_argument_and_breakdown_errors(ctx):
     x, info = msc.solve(ctx, op, p.b[0], p.sigma, max_iter=10, refine=0, raise_on_error=False)
     assert info.status == msc.MSC_ERR_NOT_CONVERGED and info.iters == 10
     assert np.all(np.isfinite(x)) and np.linalg.norm(x) > 0
+    for prec in (msc.MSC_FP64, msc.MSC_MIXED):
+        x, info = msc.solve(ctx, op, p.b[0], p.sigma, max_iter=0, precision=prec, raise_on_error=False)
+        assert info.status == msc.MSC_ERR_NOT_CONVERGED and info.iters == 0 and np.all(x == 0)
     msc.msc_op_destroy(op)
     # an indefinite operator is reported as not positive definite
     rp, ci, va, A = inputs.random_hpd_bsr(12, 2, 3, 0.5, 5)
