@@ -50,7 +50,7 @@ extern "C" {
 #define MSC_ERR_NONFINITE     5  /* NaN or Inf met in the source or the iteration */
 #define MSC_ERR_NOT_CONVERGED 6  /* iteration cap reached; x is written, see info */
 #define MSC_ERR_TIMEOUT       7  /* reserved: a bounded device wait gave up */
-#define MSC_ERR_UNSUPPORTED   8  /* valid request this build does not handle */
+#define MSC_ERR_UNSUPPORTED   8  /* valid request the library does not handle */
 #define MSC_ERR_BREAKDOWN     9  /* msc_solve_nonherm: a BiCGStab denominator vanished */
 
 /* precision of the iteration */
