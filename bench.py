@@ -47,17 +47,31 @@ SPMV_KERNEL = ("bsr.cu", "// The FP32 PASS_A of a single system",
                "template <class T, int BD, int KIND, class TO>\nstatic void launch_one(")
 
 
-def spmv_source_hash():
+def _code_only(text):
+    """C/C++ source without comments and whitespace (what the compiler sees)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return re.sub(r"\s+", "", text)
+
+
+def spmv_source_hash(read=None):
+    """Hash of the profiled kernel's code: its own text in bsr.cu (from its
+    leading comment to the next launcher template) and the headers it depends
+    on, comments and whitespace removed. `read(name)` returns a source file's
+    text (default: the working tree)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1102_2143_gb300", "csrc")
+    if read is None:
+        def read(name):
+            with open(os.path.join(csrc, name)) as f:
+                return f.read()
     h = hashlib.sha256()
     for name in SPMV_HEADERS:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
-    with open(os.path.join(csrc, SPMV_KERNEL[0])) as f:
-        src = f.read()
+        h.update(_code_only(read(name)).encode())
+    src = read(SPMV_KERNEL[0])
     a = src.index(SPMV_KERNEL[1])
-    h.update(src[a:src.index(SPMV_KERNEL[2], a)].encode())
+    h.update(_code_only(src[a:src.index(SPMV_KERNEL[2], a)]).encode())
     return h.hexdigest()
 
 
