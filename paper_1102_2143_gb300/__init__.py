@@ -7,7 +7,10 @@ library's CUDA kernels. There is no CPU fallback: if the library cannot be
 loaded, every call raises.
 
 Solves (A + sigma_s I) x_s = b for all shifts from one Krylov sequence
-(CG-M, Algorithm 1, Sec. 2 of arXiv:1102.2143).
+(CG-M, Algorithm 1, Sec. 2 of arXiv:1102.2143) for Hermitian positive-definite
+A (`solve`, `solve_batched`), and by BiCGStab-M for non-Hermitian A
+(`solve_nonherm`); `autograd.quad_form` differentiates the quadratic form
+sum_s c_s phi^dag (A + sigma_s)^{-1} phi.
 """
 from __future__ import annotations
 

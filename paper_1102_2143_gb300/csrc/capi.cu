@@ -1,13 +1,17 @@
-// C ABI of libmsc and the host driver of the multi-shift CG solve.
+// C ABI of libmsc and the host driver of the multi-shift solves.
 //
-// The solve runs CG-M (Algorithm 1, Sec. 2) entirely on the device: the
-// host only launches CUDA graphs, each holding a chunk of iterations
-// (operator pass, residual update, fused multi-shift update per iteration),
-// and reads a few bytes of status after each chunk. In mixed precision a
-// chunk ends with an FP64 reliable update of every system's base residual.
-// After the multi-shift stage the FP64 true residual of every shift is
-// measured and each shift above the tolerance is refined by a single-shift
-// solve warm-started from its x_s.
+// CG-M (Algorithm 1, Sec. 2) runs entirely on the device: the host only
+// launches CUDA graphs, each holding a chunk of iterations (operator pass,
+// residual update, fused multi-shift update per iteration), and reads a few
+// bytes of status after each chunk. In mixed precision each iteration ends
+// with a conditional graph node that runs an FP64 reliable update of a
+// system's base residual when the device decided one is due (its residual
+// fell by reliable_delta, or reliable_every iterations passed). After the
+// multi-shift stage the FP64 true residual of every shift is measured and
+// each shift above the tolerance is refined by a single-shift solve
+// warm-started from its x_s. The same driver serves batches of uneven
+// systems (msc_solve_batched) and, with its own kernels, BiCGStab-M for
+// non-Hermitian families (msc_solve_nonherm).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
