@@ -43,3 +43,40 @@ def test_binding_covers_the_header(lib_path):
     assert "positive definite" in lib.msc_strerror(4).decode()
     p = msc.msc_params_default()
     assert p.tol == 1e-10 and p.reliable_every == 50 and p.precision == msc.MSC_MIXED
+
+
+def test_header_compiles_as_c_and_links(lib_path, tmp_path):
+    """A plain C99 program includes include/msc.h, links libmsc.so and calls
+    the entry points that need no GPU (defaults, error strings) and the
+    argument checks that return before any device work."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "msc.h"
+int main(void) {
+    msc_params p;
+    msc_params_default(&p);
+    if (p.tol != 1e-10 || p.max_iter != 100000 || p.precision != MSC_MIXED ||
+        p.reliable_every != 50 || p.freeze_converged != 1 || p.refine != 4) return 1;
+    if (strcmp(msc_strerror(MSC_OK), "ok") != 0) return 2;
+    if (strlen(msc_strerror(MSC_ERR_BREAKDOWN)) == 0) return 3;
+    if (msc_solve(NULL, NULL, NULL, 1, NULL, 1, &p, NULL, NULL) != MSC_ERR_ARG) return 4;
+    if (msc_solve_nonherm(NULL, NULL, NULL, 1, NULL, 1, &p, NULL, NULL) != MSC_ERR_ARG) return 5;
+    if (msc_op_destroy(NULL) != MSC_ERR_ARG) return 6;
+    puts("abi ok");
+    return 0;
+}
+''')
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib_path)
+    cmd = [gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+           "-L", libdir, "-lmsc", "-Wl,-rpath," + libdir, "-o", str(exe)]
+    subprocess.run(cmd, check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and "abi ok" in out.stdout, (out.returncode, out.stderr)
