@@ -113,7 +113,7 @@ def spmv_bytes(nnzb, bd, n, real_bytes):
     return nnzb * (bd * bd * 2 * real_bytes + 4) + 2 * n * 2 * real_bytes
 
 
-def solve_bytes(info, S, nnzb, bd, n, mixed=True, reliable_every=50, group=8):
+def solve_bytes(info, S, nnzb, bd, n, mixed=True):
     """Algorithmic HBM bytes of one solve, from what it ran.
 
     c = bytes of one complex unknown in the iteration precision (8 mixed,
@@ -129,8 +129,8 @@ def solve_bytes(info, S, nnzb, bd, n, mixed=True, reliable_every=50, group=8):
       one FP64 residual SpMV (+ b read, r write).
     Checks: each check round applies the FP64 operator to every shift it
       checks (round 0: all S; later rounds: the shifts just refined).
-    Refinement iteration k: the SpMV reads the matrix once per group of
-      `group` refined shifts with one still iterating, plus source and output
+    Refinement iteration k: the SpMV reads the matrix once for all refined
+      shifts still iterating (they share one launch), plus source and output
       per iterating shift; r update 3 passes and update 5 passes per shift.
     """
     rb = 4 if mixed else 8
@@ -162,9 +162,8 @@ def solve_bytes(info, S, nnzb, bd, n, mixed=True, reliable_every=50, group=8):
     total += (S + refined * int(info.refine_rounds)) * a64
     kmax = int(ref.max()) if len(ref) else 0
     for k in range(1, kmax + 1):
-        act = [s for s in range(len(ref)) if ref[s] >= k]
-        groups = len({s // group for s in act})
-        total += groups * mat + len(act) * (2 + 3 + 5) * n * c
+        act = int(np.count_nonzero(ref >= k))
+        total += mat + act * (2 + 3 + 5) * n * c
     return total
 
 
