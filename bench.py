@@ -675,6 +675,9 @@ def main():
     msc.msc_op_destroy(op)
     msc.msc_destroy(ctx)
     if pg is not None:
+        # the other ranks wait for rank 0's secondary workloads, then all
+        # leave together
+        barrier(pg, torch)
         pg.destroy_process_group()
     return 0
 
