@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/msc.h"
 #include "bicgstab.cuh"
 #include "engine.h"
@@ -48,6 +50,15 @@ struct GraphEntry {
 };
 
 long g_op_uid = 0;
+
+// A named range on the profiler timeline for the lifetime of the object (a
+// no-op unless a profiling tool is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 }  // namespace
 
@@ -942,6 +953,7 @@ int msc_op_dslash(msc_ctx* c, const msc_op* op, const double* in, double* out) {
 int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const double* sigma, int S,
               const msc_params* prm_in, double* x, msc_info* info) {
     const auto t0 = std::chrono::steady_clock::now();
+    const Range whole("msc_solve");
     if (!c || !op || !b || !x || !sigma || nrhs <= 0 || S <= 0 || S > kMaxShifts) return MSC_ERR_ARG;
     msc_params prm;
     msc_params_default(&prm);
@@ -1015,7 +1027,10 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     const int chunk = 25;
     ProfAcc pa;
     int rel = 0, rel_ref = 0;
-    st = run_stage(c, op, prec, nrhs, chunk, mixed, true, npad, prm.max_iter, &pa, &rel);
+    {
+        const Range stage("msc_solve: multi-shift stage");
+        st = run_stage(c, op, prec, nrhs, chunk, mixed, true, npad, prm.max_iter, &pa, &rel);
+    }
     if (st) return st;
     int status = MSC_OK;
     int iters = 0;
@@ -1047,6 +1062,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         std::vector<int> todo(nslots);
         for (int g = 0; g < nslots; ++g) todo[g] = g;
         for (int round = 0; !todo.empty(); ++round) {
+            const Range rr("msc_solve: FP64 check and refinement round");
             const bool check_only = round >= prm.refine;
             const int m = (int)todo.size();
             for (int k = 0; k < m; ++k) {
@@ -1161,6 +1177,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
 int msc_solve_nonherm(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const double* sigma, int S,
                       const msc_params* prm_in, double* x, msc_info* info) {
     const auto t0 = std::chrono::steady_clock::now();
+    const Range whole("msc_solve_nonherm");
     if (!c || !op || !b || !x || !sigma || nrhs <= 0 || S <= 0 || S > kMaxShifts) return MSC_ERR_ARG;
     msc_params prm;
     msc_params_default(&prm);
@@ -1653,6 +1670,7 @@ static int autotune_batch(msc_ctx* c, int prec, const BatchHost& bh, const std::
 extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs, const msc_params* prm_in,
                                  msc_tuning* tuning) {
     const auto t0 = std::chrono::steady_clock::now();
+    const Range whole("msc_solve_batched");
     if (!c || nprob <= 0 || !probs) return MSC_ERR_ARG;
     msc_params prm;
     msc_params_default(&prm);
@@ -2034,6 +2052,7 @@ extern "C" int msc_quad_form(msc_ctx* c, const msc_op* op, const double* phi, in
 
 extern "C" int msc_quad_form_grad(msc_ctx* c, const msc_op* op, int S, const double* coef,
                                   const double* x, double* dphi, double* dU) {
+    const Range whole("msc_quad_form_grad");
     if (!c || !op || !coef || !x || S <= 0 || (!dphi && !dU)) return MSC_ERR_ARG;
     if (dU && op->dev.kind != OP_STAGGERED) return MSC_ERR_ARG;
     int st = begin(c);
