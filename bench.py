@@ -177,6 +177,83 @@ def multishift_iter_bytes_fp64(S, nnzb, bd, n):
     return spmv_bytes(nnzb, bd, n, 8) + (3 + 3 + 4 * (S - 1) + 2) * n * 16
 
 
+def stencil_solve_bytes(info, S, V, nc, recon, mixed=True):
+    """Algorithmic HBM bytes of one solve through the staggered stencil path
+    (msc_solve on a staggered operator, nrhs right-hand sides), from what it
+    ran. u = bytes of one site's colour vector in the iteration precision
+    (8 nc mixed, 16 nc FP64); l = bytes of one site's FP32 links in the four
+    directions ((nc-1) nc complex with row reconstruction, else nc^2), l64
+    the FP64 links (nc^2 complex). A D pass reads every link once whatever
+    the number of right-hand sides it serves (they share the links).
+    Multi-shift iteration k (R_k right-hand sides still iterating):
+      pass 1 (t = D p, P): links + R_k (p read, t write);
+      pass 2 (r -= alpha (d p - D t), |r|^2): links + R_k (t, p, r read, r write);
+      update: per right-hand side r, p read + p write, the base shift's x
+      read + write, and per non-base shift still iterating x_s, p_s read +
+      write (x_s and p_s read + x_s write in its last iteration).
+    Mixed only, per reliable update (count reported): fold every shift of
+    that right-hand side (x32 read, x64 read + write) and one FP64 residual
+    (two FP64 D passes: links64 twice, x64 read, t64 write, t64, x64, b read,
+    r write); the stage's final fold of every shift.
+    Checks and refinement as in `solve_bytes`, with two FP64 D passes per
+    residual and, per refinement iteration, the links once per pass for all
+    refined shifts still iterating plus 2 + 4 + 5 vector passes per shift.
+    """
+    rb = 4 if mixed else 8
+    u = 2 * rb * nc
+    l = 4 * ((nc - 1) if (mixed and recon) else nc) * nc * 2 * rb
+    l64 = 4 * nc * nc * 16
+    u64 = 16 * nc
+    res64 = 2 * l64 + 2 * u64 + 3 * u64 + u   # one FP64 residual b - (A + s) x, per site
+    it_all = np.asarray(info.shift_iters).reshape(-1, S)
+    R = it_all.shape[0]
+    total = 0.0
+    for r in range(R):
+        conv = it_all[r]
+        base = int(np.argmax(conv))
+        itr = int(conv.max())
+        for k in range(1, itr + 1):
+            upd = 3 + 2
+            for s_, cv in enumerate(conv):
+                if s_ == base:
+                    continue
+                upd += 4 if k < cv else (3 if k == cv else 0)
+            total += V * (2 * u + 4 * u + upd * u)
+    iters = int(info.iters)
+    total += iters * 2 * V * l  # links of both passes, shared by the right-hand sides
+    if mixed:
+        ru_main = int(info.reliable_updates) - int(info.refine_reliable_updates)
+        fold = 40 * nc * V
+        total += (ru_main + R) * S * fold
+        total += ru_main * V * res64
+        total += int(info.refine_reliable_updates) * V * (res64 + fold)
+    ref = np.asarray(info.shift_refine_iters).reshape(-1)
+    refined = int(np.count_nonzero(ref))
+    total += (R * S + refined * int(info.refine_rounds)) * V * res64
+    kmax = int(ref.max()) if len(ref) else 0
+    for k in range(1, kmax + 1):
+        act = int(np.count_nonzero(ref >= k))
+        total += 2 * V * l + act * V * (2 + 4 + 5) * u
+    return total
+
+
+def stencil_pass_fracs(info, V, nc, recon, nrhs, peak):
+    """Live fractions of HBM of the two D passes and the update kernel at the
+    sampled multi-shift iterations (every right-hand side iterating):
+    algorithmic bytes of one launch / its mean CUDA-event time."""
+    u, l = 8 * nc, 4 * ((nc - 1) if recon else nc) * nc * 8
+    b1 = V * (l + nrhs * 2 * u)
+    b2 = V * (l + nrhs * 4 * u)
+    bu = V * u * (5 * nrhs + 4 * float(info.prof_active))
+    out = {"pass1_bytes": b1, "pass2_bytes": b2, "update_bytes": bu,
+           "pass1_ms": info.op_ms, "pass2_ms": info.rupdate_ms, "update_ms": info.update_ms,
+           "update_active_shifts": float(info.prof_active)}
+    for k, b, ms in (("pass1", b1, info.op_ms), ("pass2", b2, info.rupdate_ms), ("update", bu, info.update_ms)):
+        out[k + "_gbs"] = b / (ms * 1e-3) / 1e9 if ms else None
+        out[k + "_frac"] = out[k + "_gbs"] / peak if ms else None
+    return out
+
+
 # ----------------------------------------------------------------------------
 # helpers
 # ----------------------------------------------------------------------------
@@ -296,13 +373,25 @@ def oracle_sample(problem, iters):
     return dt, oracle.num_threads()
 
 
-def cpu_line(problem, nnzb, bd, n, S, iters):
+def cpu_line(problem, nnzb, bd, n, S, iters, iters_1core=2):
+    import oracle
     dt, cores = oracle_sample(problem, iters)
     b = multishift_iter_bytes_fp64(S, nnzb, bd, n) * iters
-    return {"value": b / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "ms_per_iteration": 1e3 * dt / iters,
-            "sample": f"{iters} CG-M iterations (FP64, all {S} shifts active) of the full "
-                      f"24^4 workload, stencil form of the same A"}
+    out = {"value": b / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+           "ms_per_iteration": 1e3 * dt / iters,
+           "sample": f"{iters} CG-M iterations (FP64, all {S} shifts active) of the full "
+                     f"24^4 workload, stencil form of the same A"}
+    # the same on one host core (the paper's CPU figure is one core)
+    oracle.set_threads(1)
+    try:
+        dt1, _ = oracle_sample(problem, iters_1core)
+    finally:
+        oracle.set_threads(cores)
+    b1 = multishift_iter_bytes_fp64(S, nnzb, bd, n) * iters_1core
+    out["one_core"] = {"value": b1 / dt1 / 1e9, "unit": "GB/s", "cores": 1,
+                       "ms_per_iteration": 1e3 * dt1 / iters_1core,
+                       "sample": f"{iters_1core} CG-M iterations, same workload, one thread"}
+    return out
 
 
 def run_reference(args):
@@ -383,6 +472,15 @@ def paper_workload(ctx, msc, inputs, torch, stream):
     out["cgm_15_shifts_fp64"] = timed(p.sigma, msc.MSC_FP64)
     out["cgm_15_shifts_mixed"] = timed(p.sigma, msc.MSC_MIXED)
     out["cg_unshifted_fp64"] = timed(np.array([0.0]), msc.MSC_FP64)
+    # the paper's comparison: the 15 shifted systems solved one by one
+    # (single-shift CG each) against one CG-M solve of all of them
+    for prec, name in ((msc.MSC_FP64, "fp64"), (msc.MSC_MIXED, "mixed")):
+        sep = [timed(np.array([sg]), prec) for sg in p.sigma]
+        tot = sum(r["time_to_solution_ms"] for r in sep)
+        out[f"separate_cg_15_shifts_{name}"] = {
+            "time_to_solution_ms": tot, "iterations": sum(r["iterations"] for r in sep),
+            "max_true_rel_resid": max(r["max_true_rel_resid"] for r in sep),
+            "cgm_speedup": tot / out[f"cgm_15_shifts_{name}"]["time_to_solution_ms"]}
     out["cgm_15_fp64_speedup_per_iteration_vs_t10"] = (
         PAPER_T10["cgm_15_shifts_gpu_fp64"] / out["cgm_15_shifts_fp64"]["ms_per_iteration"])
     msc.msc_op_destroy(op)
@@ -401,6 +499,125 @@ def stencil_pass_bytes(V, nc, recon):
     link = 4 * (nc - 1 if recon else nc) * nc * 8
     vec = nc * 8
     return V * (link + 2 * vec), V * (link + 4 * vec)
+
+
+LARGEST = ("32^4 SU(3) staggered A=M^dag M (stencil, two-row FP32 links), m=0.01, eps=0.9, "
+           "20 shifts 1e-5..10, 8 Gaussian RHS, mixed FP32/FP64, reliable updates every 50 "
+           "iterations at the latest, tol 1e-10 FP64 true residual per shift")
+
+
+def largest_config(ctx, msc, inputs, torch, stream, steps=2, fp64=True):
+    """The largest workload that fits one GPU, measured like the headline:
+    time to solution of all 160 shifted systems, algorithmic GB/s of the
+    whole solve, the live fractions of the two D passes and the update
+    kernel, end to end through the C ABI with host buffers, and the plain
+    FP64 form of the same solve."""
+    peak, peak_kind = load_peaks()
+    p = inputs.lattice_32x4_su3_20shifts()
+    V, S, R = inputs.volume(p.dims), len(p.sigma), p.b.shape[0]
+    op = msc.msc_op_staggered(ctx, p.nc, p.dims, torch.from_numpy(p.links).cuda(), p.mass)
+    recon = msc.msc_op_recon(op)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.empty((R, S, p.n), dtype=torch.complex128, device="cuda")
+
+    def run(bb, xx, prec=msc.MSC_MIXED):
+        _, info = msc.solve(ctx, op, bb, p.sigma, x=xx, tol=p.tol, precision=prec)
+        assert info.status == 0, info.status
+        return info
+
+    run(b, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [run(b, x) for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    info = infos[-1]
+    nbytes = stencil_solve_bytes(info, S, V, p.nc, recon)
+    fr = stencil_pass_fracs(info, V, p.nc, recon, R, peak)
+    out = {"workload": LARGEST, "steps": steps, "time_to_solution_ms": ms,
+           "value": nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "frac_of_peak": nbytes / (ms * 1e-3) / 1e9 / peak,
+           "algorithmic_bytes": nbytes, "iterations": info.iters, "refine_iterations": info.refine_iters,
+           "refine_system_iterations": int(np.sum(info.shift_refine_iters)),
+           "reliable_updates": info.reliable_updates,
+           "iters_per_s": (info.iters + info.refine_iters) / (ms * 1e-3),
+           "max_true_rel_resid": float(np.max(info.true_rel_resid)), "gpu_launches": info.kernel_launches,
+           "kernels_live": fr, "peak": peak, "peak_source": peak_kind,
+           "timing": "CUDA events on the solve's stream; pass and update times sampled inside the solve's graphs"}
+    roof = []
+    for k, kern in (("pass1", "k_stag_group PASS_A (t = D p, P fused; links once per group of right-hand sides)"),
+                    ("pass2", "k_stag_group PASS_B (r -= alpha (d p - D t), |r|^2 fused)"),
+                    ("update", "k_update (fused multi-shift update)")):
+        if fr[k + "_gbs"]:
+            roof.append({"kernel": kern, "bound": "hbm", "achieved": fr[k + "_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": fr[k + "_frac"], "bytes_per_launch": fr[k + "_bytes"], "launch_ms": fr[k + "_ms"]})
+    out["roofline"] = roof
+    # end to end: pinned host source and solution
+    bh = torch.from_numpy(p.b).pin_memory()
+    xh = torch.empty((R, S, p.n), dtype=torch.complex128).pin_memory()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ie = run(bh, xh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e = e0.elapsed_time(e1)
+    out["e2e"] = {"value": stencil_solve_bytes(ie, S, V, p.nc, recon) / (ms_e * 1e-3) / 1e9, "unit": "GB/s",
+                  "ms_per_step": ms_e, "h2d_bytes_per_step": R * p.n * 16, "d2h_bytes_per_step": R * S * p.n * 16}
+    del xh, bh
+    if fp64:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        i64 = run(b, x, msc.MSC_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        out["fp64_plain"] = {"time_to_solution_ms": ms64, "iterations": i64.iters,
+                             "value": stencil_solve_bytes(i64, S, V, p.nc, recon, mixed=False) / (ms64 * 1e-3) / 1e9,
+                             "unit": "GB/s", "pass1_fp64_ms": i64.op_ms, "pass2_fp64_ms": i64.rupdate_ms,
+                             "max_true_rel_resid": float(np.max(i64.true_rel_resid))}
+        out["speedup_vs_fp64_plain"] = ms64 / ms
+    # the same source restricted to even sites through the single-parity solve
+    # against the full-lattice solve of the embedded source (one right-hand side)
+    msc.msc_op_destroy(op)
+    del x, b
+    return out
+
+
+def parity_workload(ctx, msc, inputs, torch, stream):
+    """A source on the even sites of the 32^4 lattice (20 shifts, 1 RHS): the
+    single-parity solve on half the unknowns against msc_solve on the
+    embedded full-lattice source."""
+    p = inputs.lattice_32x4_su3_20shifts(nrhs=1)
+    V, S = inputs.volume(p.dims), len(p.sigma)
+    op = msc.msc_op_staggered(ctx, p.nc, p.dims, torch.from_numpy(p.links).cuda(), p.mass)
+    x = np.arange(V)
+    c = [x % p.dims[0], (x // p.dims[0]) % p.dims[1], (x // (p.dims[0] * p.dims[1])) % p.dims[2],
+         x // (p.dims[0] * p.dims[1] * p.dims[2])]
+    even = np.nonzero(((c[0] + c[1] + c[2] + c[3]) & 1) == 0)[0]
+    bh = p.b[0].reshape(V, p.nc)[even].reshape(-1)
+    bf = np.zeros((V, p.nc), dtype=np.complex128)
+    bf[even] = bh.reshape(-1, p.nc)
+    bh_d = torch.from_numpy(bh).cuda()
+    bf_d = torch.from_numpy(bf.reshape(-1)).cuda()
+    out = {"workload": "32^4 SU(3), m=0.01, eps=0.9, 20 shifts 1e-5..10, one Gaussian source on the even "
+                       "sites, mixed, tol 1e-10"}
+    for name, fn in (("full_lattice", lambda: msc.solve(ctx, op, bf_d, p.sigma, tol=p.tol)),
+                     ("single_parity", lambda: msc.solve_parity(ctx, op, 0, bh_d, p.sigma, tol=p.tol))):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, info = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert info.status == 0, info.status
+        out[name] = {"time_to_solution_ms": e0.elapsed_time(e1), "iterations": info.iters,
+                     "refine_iterations": info.refine_iters, "pass1_ms": info.op_ms, "pass2_ms": info.rupdate_ms,
+                     "update_ms": info.update_ms, "max_true_rel_resid": float(np.max(info.true_rel_resid))}
+    out["speedup"] = out["full_lattice"]["time_to_solution_ms"] / out["single_parity"]["time_to_solution_ms"]
+    msc.msc_op_destroy(op)
+    return out
 
 
 def other_workloads(ctx, msc, inputs, torch, stream):
@@ -449,10 +666,16 @@ def other_workloads(ctx, msc, inputs, torch, stream):
     ms_b, (_, infos, tun) = ev_time(lambda: msc.solve_batched(ctx, items))
     ms_s, _ = ev_time(lambda: [msc.solve(ctx, o, bb, sg) for o, bb, sg in items])
     assert all(i.status == 0 for i in infos)
+    bbytes = sum(stencil_solve_bytes(i, len(q.sigma), inputs.volume(q.dims), q.nc, msc.msc_op_recon(o))
+                 for i, q, o in zip(infos, probs, ops))
     out["batched_64_uneven_mixed"] = {
         "workload": "64 staggered problems, L in {4..12}, SU(2)/SU(3), m in [0.02,0.2], eps=0.6, "
                     "4..20 shifts 1e-4..1, 4 RHS each, mixed, tol 1e-10",
         "batched_ms": ms_b, "one_by_one_ms": ms_s, "speedup": ms_s / ms_b,
+        "algorithmic_bytes": bbytes, "batched_gbs": bbytes / (ms_b * 1e-3) / 1e9,
+        "batched_frac": bbytes / (ms_b * 1e-3) / 1e9 / peak,
+        "one_by_one_gbs": bbytes / (ms_s * 1e-3) / 1e9,
+        "bytes": "sum over the 64 problems of the stencil solve's algorithmic bytes (bench.stencil_solve_bytes)",
         "tuned_shape": {"site_threads": tun.site_threads, "vec_threads": tun.vec_threads,
                         "vec_units": tun.vec_units}}
     for o in ops:
@@ -525,6 +748,11 @@ def main():
     ap.add_argument("--no-paper", action="store_true",
                     help="skip the paper's own 2-D Poisson workload (context numbers)")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-largest", action="store_true",
+                    help="skip the largest single-GPU workload (32^4, 8 RHS, 20 shifts)")
+    ap.add_argument("--largest-steps", type=int, default=2)
+    ap.add_argument("--no-fp64-largest", action="store_true",
+                    help="skip the plain FP64 form of the largest workload")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the device-timed steps with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
@@ -602,11 +830,19 @@ def main():
     roof = None
     if spmv_ms:
         ach = spmv_b / (spmv_ms * 1e-3) / 1e9
+        # the fused multi-shift update at the same sampled iterations: r, p
+        # read, p write, the base shift's x read + write, and x_s, p_s read +
+        # write for every non-base shift still iterating (count sampled live)
+        upd_ms = float(np.mean([i.update_ms for i in infos]))
+        upd_act = float(np.mean([i.prof_active for i in infos]))
+        upd_b = (5 + 4 * upd_act) * n * 8
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": load_spmv_traffic(), "kernel": "k_bsr_a1<3> (FP32 SpMV + fused P)",
                 "bytes_per_launch": spmv_b, "launch_ms": spmv_ms, "peak_source": peak_kind,
-                "update_kernel_ms": float(np.mean([i.update_ms for i in infos])),
-                "rupdate_kernel_ms": float(np.mean([i.rupdate_ms for i in infos]))}
+                "update_kernel_ms": upd_ms, "update_active_shifts": upd_act, "update_bytes_per_launch": upd_b,
+                "update_frac": upd_b / (upd_ms * 1e-3) / 1e9 / peak if upd_ms else None,
+                "rupdate_kernel_ms": float(np.mean([i.rupdate_ms for i in infos])),
+                "rupdate_frac": 3 * n * 8 / (float(np.mean([i.rupdate_ms for i in infos])) * 1e-3) / 1e9 / peak}
 
     # ---- end to end: host source and solution buffers ------------------------
     barrier(pg, torch)
@@ -640,6 +876,12 @@ def main():
     aux = None
     if rank == 0 and not args.no_aux:
         aux = other_workloads(ctx, msc, inputs, torch, stream)
+        aux["single_parity_32x4_20shifts"] = parity_workload(ctx, msc, inputs, torch, stream)
+
+    largest = None
+    if rank == 0 and not args.no_largest:
+        largest = largest_config(ctx, msc, inputs, torch, stream, steps=args.largest_steps,
+                                 fp64=not args.no_fp64_largest)
 
     paper = None
     if rank == 0 and not args.no_paper:
@@ -668,7 +910,7 @@ def main():
             "max_true_rel_resid": float(np.max(last.true_rel_resid)),
             "fp64_plain": fp64, "speedup_vs_fp64_plain": f_ms / ms,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
-            "paper_workload": paper, "other_workloads": aux,
+            "paper_workload": paper, "other_workloads": aux, "largest_config": largest,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -63,8 +63,12 @@ extern "C" {
 #define MSC_FP32  2  /* msc_op_apply only: the FP32 operator kernel */
 
 /* operator flags */
-#define MSC_LINKS_FULL  1u  /* keep all Nc*Nc FP32 link entries (no SU(N)
-                               row reconstruction), e.g. for non-unitary links */
+#define MSC_LINKS_FULL  1u  /* msc_op_staggered: keep all Nc*Nc FP32 link entries
+                               (no SU(N) row reconstruction), e.g. for
+                               non-unitary links */
+#define MSC_CHECK_HERMITIAN 2u /* msc_op_bsr: check on the device at creation
+                               that A is Hermitian (CG-M needs A = A^dagger,
+                               eq. linprob, Sec. 2); see msc_op_bsr */
 
 typedef struct msc_ctx msc_ctx;
 typedef struct msc_op msc_op;
@@ -92,11 +96,20 @@ int msc_op_staggered(msc_ctx* ctx, msc_op** op, int nc, const int dims[4],
 /* Generic block-CSR operator: nbr block rows of complex bd x bd blocks
  * (bd = 1, 2 or 3), row_ptr[nbr+1] (int64, non-decreasing, row_ptr[0] = 0),
  * col_idx[nnzb] (int32 in [0, nbr)), vals[nnzb][bd][bd] complex FP64.
- * Repeated block columns in a row add. A must be Hermitian positive
- * definite; this is not checked here (the solve reports MSC_ERR_NOT_HPD
- * when it meets p^dagger A p <= 0). n = nbr * bd. A block row may hold
- * at most 2^26 / (bd * bd) blocks (about 7.4 million 3 x 3 blocks);
- * longer rows, like any other malformed input, give MSC_ERR_ARG. */
+ * Repeated block columns in a row add. msc_solve needs A Hermitian
+ * positive definite (CG-M, Sec. 2); msc_solve_nonherm takes any A.
+ * flags: 0 or MSC_CHECK_HERMITIAN (other bits give MSC_ERR_ARG). With
+ * MSC_CHECK_HERMITIAN a device kernel forms every entry A_ij (repeated
+ * columns summed) and its partner A_ji and the call fails with
+ * MSC_ERR_NOT_HPD, creating nothing, unless
+ *     max |A_ij - conj(A_ji)| <= 1e-12 * max |A_ij|
+ * over all entries (a block whose transposed partner is not stored counts
+ * against a zero partner); its cost is, per stored block, the length of
+ * its row and of its column's row. Without the flag Hermiticity is not
+ * checked; positivity is never checked here (the solve reports
+ * MSC_ERR_NOT_HPD when it meets p^dagger A p <= 0). n = nbr * bd. A block
+ * row may hold at most 2^26 / (bd * bd) blocks (about 7.4 million 3 x 3
+ * blocks); longer rows, like any other malformed input, give MSC_ERR_ARG. */
 int msc_op_bsr(msc_ctx* ctx, msc_op** op, int64_t nbr, int bd, const int64_t* row_ptr,
                const int32_t* col_idx, const double* vals, unsigned flags);
 
@@ -138,8 +151,9 @@ int msc_op_destroy(msc_op* op);
  * library (256 bytes + 16 MiB, held on every device that loads the library
  * until the process exits), so n may be at most 2^20 complex unknowns;
  * larger operators get MSC_ERR_ARG, block-CSR operators MSC_ERR_UNSUPPORTED.
- * in and out are device pointers on the operator's device ([n] complex,
- * out may equal in). The work is queued on `stream` (a cudaStream_t, NULL
+ * in and out are device pointers on the operator's device, or managed
+ * memory ([n] complex, out may equal in); device memory of another GPU or
+ * host memory gives MSC_ERR_ARG before anything is launched. The work is queued on `stream` (a cudaStream_t, NULL
  * for the legacy default stream) and the call returns without waiting;
  * out is ready when the stream reaches that point. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with
@@ -199,9 +213,16 @@ typedef struct {
                   fused |r|^2; staggered: second D pass with r -= alpha Ap
                   and |r|^2 fused),
        update_ms  the fused multi-shift update kernel;
-       prof_samples the number of samples (0: not measured) */
+       prof_samples the number of samples (0: not measured);
+       prof_active  the mean, over the samples, of the number of non-base
+                  shifts (summed over right-hand sides) still iterating at
+                  the sampled iteration: the sampled update kernel moved
+                  r, p (read) and p (write) and the base shift's x (read
+                  and write) per right-hand side, and x_s and p_s (read
+                  and write) per such shift */
     double op_ms, rupdate_ms, update_ms;
     int prof_samples;
+    double prof_active;
 } msc_info;
 
 /* Solve (A + sigma_s) x_{r,s} = b_r for every shift s and right-hand side r.
@@ -212,6 +233,48 @@ typedef struct {
 int msc_solve(msc_ctx* ctx, const msc_op* op, const double* b, int nrhs,
               const double* sigma, int S, const msc_params* params, double* x,
               msc_info* info);
+
+/* The shifted family for a source on the sites of one parity (staggered
+ * operators): A = m^2 - D^2 couples no even site to an odd one (D hops one
+ * site, so D^2 keeps the parity), so for b zero on the sites of parity
+ * 1 - p the solution is zero there too and its parity-p part solves
+ *     (m^2 - D_{p,1-p} D_{1-p,p} + sigma_s) x_s = b
+ * on half the unknowns: every vector pass of the iteration moves half the
+ * bytes of msc_solve on the embedded source (the links are still read
+ * once per D pass). parity: 0 for even sites ((x0+x1+x2+x3) mod 2 = 0), 1
+ * for odd. b: [nrhs][V/2][nc] and x: [nrhs][S][V/2][nc] complex, the
+ * parity-p sites in increasing site order (site x at index x / 2). A
+ * standard optimisation of staggered solvers, not in the paper. Other
+ * arguments, the refinement and errors as in msc_solve; info->true_rel_resid
+ * is |b - (A + sigma_s) x_s| / |b| over the parity-p sites (the whole
+ * lattice's, since both vanish on the other parity). */
+int msc_solve_parity(msc_ctx* ctx, const msc_op* op, int parity, const double* b, int nrhs,
+                     const double* sigma, int S, const msc_params* params, double* x,
+                     msc_info* info);
+
+/* Different right-hand side per shift (Sec. 5, eq. linprobgen), for
+ * right-hand sides of polynomial form in A:
+ *     (A + sigma_s) x_s = b_s,   b_s = q_s(A) b,
+ *     q_s(t) = sum_{k=0}^{deg} coef[s * (deg + 1) + k] t^k   (real coefficients).
+ * The paper points to initial guesses x_s0 that make the shifted residuals
+ * collinear, so that one CG-M sequence serves every shift; for this form
+ * they follow from dividing q_s(t) by (t + sigma_s):
+ *     q_s(t) = q_s(-sigma_s) + (t + sigma_s) s_s(t),   x_s0 = s_s(A) b,
+ *     b_s - (A + sigma_s) x_s0 = q_s(-sigma_s) b,
+ * so x_s = x_s0 + q_s(-sigma_s) (A + sigma_s)^{-1} b: one CG-M solve on b
+ * (each shift stopping at |b - (A+sigma_s) z_s| <= tol |b_s| / |q_s(-sigma_s)|)
+ * plus deg - 1 FP64 operator applications per shift for x_s0 and deg for
+ * b_s. The FP64 true residual |b_s - (A + sigma_s) x_s| / |b_s| of every
+ * shift is then checked and refined to tol exactly as in msc_solve.
+ * b: [n] complex (one source); sigma: [S] host, each >= 0; coef: [S][deg+1]
+ * host, finite; 0 <= deg <= MSC_MAX_POLY_DEGREE; x: [S][n] complex out. A
+ * shift whose b_s is zero gets x_s = 0. info arrays hold S entries;
+ * info->true_rel_resid is relative to |b_s|. Other arguments and errors as
+ * in msc_solve. */
+#define MSC_MAX_POLY_DEGREE 32
+int msc_solve_poly_rhs(msc_ctx* ctx, const msc_op* op, const double* b, const double* sigma, int S,
+                       const double* coef, int deg, const msc_params* params, double* x,
+                       msc_info* info);
 
 /* Non-Hermitian shifted families: (A + sigma_s I) x_{r,s} = b_r for every
  * shift by multi-shift BiCGStab (BiCGStab-M), the solver the paper names for

@@ -308,3 +308,41 @@ def link_force(links, dims, nc, c, x) -> np.ndarray:
 def quad_form(b, x, c) -> float:
     """S = sum_s c_s Re(phi^dagger x_s)."""
     return float(sum(float(c[s]) * np.vdot(b, x[s]).real for s in range(len(c))))
+
+
+# ----------------------------------------------------------------------------
+# Different right-hand side per shift (Sec. 5, eq. linprobgen), for
+# right-hand sides of polynomial form b_s = q_s(A) b. Written from the
+# definition: each b_s is formed by Horner's rule with the FP64 operator and
+# each shift is solved on its own by textbook CG.
+# ----------------------------------------------------------------------------
+
+def poly_apply_staggered(links, dims, nc, mass, coef, b) -> np.ndarray:
+    """q(A) b with q(t) = sum_k coef[k] t^k (coef[0] the constant term), by
+    Horner's rule: v = coef[d] b, then v = A v + coef[k] b for k = d-1 .. 0."""
+    coef = np.asarray(coef, dtype=np.float64)
+    b = _c128(b)
+    v = coef[-1] * b
+    for a in coef[-2::-1]:
+        v = staggered_apply(links, dims, nc, mass, v) + a * b
+    return v
+
+
+def solve_poly_rhs_staggered(links, dims, nc, mass, b, sigma, coef, tol, max_iter=100000):
+    """x_s = (A + sigma_s)^{-1} q_s(A) b for every shift s (coef: [S][deg+1]),
+    each by textbook CG from x = 0 to |b_s - (A + sigma_s) x_s| <= tol |b_s|.
+    Returns (x [S][n], b_s [S][n])."""
+    sig = np.asarray(sigma, dtype=np.float64)
+    coef = np.asarray(coef, dtype=np.float64).reshape(sig.shape[0], -1)
+    xs, bs = [], []
+    for s in range(sig.shape[0]):
+        bq = poly_apply_staggered(links, dims, nc, mass, coef[s], b)
+        if np.linalg.norm(bq) == 0.0:
+            x = np.zeros_like(bq)
+        else:
+            x, _, st = cg_staggered(links, dims, nc, mass, bq, sig[s], tol, max_iter)
+            if st != 0:
+                raise RuntimeError(f"oracle CG for shift {s}: {STATUS.get(st, st)}")
+        xs.append(x)
+        bs.append(bq)
+    return np.array(xs), np.array(bs)

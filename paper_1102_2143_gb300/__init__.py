@@ -40,6 +40,7 @@ MSC_FP64 = 0
 MSC_MIXED = 1
 MSC_FP32 = 2
 MSC_LINKS_FULL = 1
+MSC_CHECK_HERMITIAN = 2
 
 _lib = None
 _lock = threading.Lock()
@@ -66,7 +67,8 @@ class msc_info(ctypes.Structure):
                 ("shift_refine_iters", ctypes.POINTER(ctypes.c_int)),
                 ("true_rel_resid", ctypes.POINTER(ctypes.c_double)),
                 ("op_ms", ctypes.c_double), ("rupdate_ms", ctypes.c_double),
-                ("update_ms", ctypes.c_double), ("prof_samples", ctypes.c_int)]
+                ("update_ms", ctypes.c_double), ("prof_samples", ctypes.c_int),
+                ("prof_active", ctypes.c_double)]
 
 
 class msc_problem(ctypes.Structure):
@@ -104,6 +106,10 @@ SIGNATURES = {
                        ctypes.POINTER(msc_info)]),
     "msc_solve_nonherm": (_I, [_VP, _VP, _VP, _I, _VP, _I, ctypes.POINTER(msc_params), _VP,
                        ctypes.POINTER(msc_info)]),
+    "msc_solve_poly_rhs": (_I, [_VP, _VP, _VP, _VP, _I, _VP, _I, ctypes.POINTER(msc_params), _VP,
+                                ctypes.POINTER(msc_info)]),
+    "msc_solve_parity": (_I, [_VP, _VP, _I, _VP, _I, _VP, _I, ctypes.POINTER(msc_params), _VP,
+                              ctypes.POINTER(msc_info)]),
     "msc_strerror": (ctypes.c_char_p, [_I]),
     "msc_quad_form": (_I, [_VP, _VP, _VP, _I, _VP, _VP, ctypes.POINTER(_D)]),
     "msc_quad_form_grad": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
@@ -234,7 +240,24 @@ def msc_op_dslash(ctx: int, op: int, x, out) -> None:
 
 def msc_op_apply_noalloc(op: int, sigma: float, x, out, stream=None) -> None:
     """out = (A + sigma) x without any allocation (device pointers; queued on
-    `stream`, returns without waiting)."""
+    `stream`, returns without waiting).
+
+    The library takes no length here and stages nothing, so a torch tensor
+    must be a contiguous complex128 CUDA tensor of exactly n entries (n the
+    operator's size), x and out on the same device; anything else raises
+    before the call. Raw integer addresses are passed through unchecked."""
+    tensors = [a for a in (x, out) if hasattr(a, "data_ptr")]
+    if tensors:
+        import torch
+        n = msc_op_size(op)
+        for a in tensors:
+            if a.dtype != torch.complex128 or not a.is_contiguous() or not a.is_cuda:
+                raise ValueError("msc_op_apply_noalloc: x and out must be contiguous complex128 "
+                                 "CUDA tensors")
+            if a.numel() != n:
+                raise ValueError(f"msc_op_apply_noalloc: {a.numel()} entries, the operator has {n}")
+        if len({a.device for a in tensors}) > 1:
+            raise ValueError("msc_op_apply_noalloc: x and out are on different devices")
     _check(load().msc_op_apply_noalloc(op, float(sigma), _ptr(x), _ptr(out), _stream_handle(stream)),
            "msc_op_apply_noalloc")
 
@@ -295,6 +318,22 @@ def msc_solve_nonherm(ctx: int, op: int, b, nrhs: int, sigma, S: int, params: ms
                                     ctypes.byref(info) if info is not None else None)
 
 
+def msc_solve_poly_rhs(ctx: int, op: int, b, sigma, S: int, coef, deg: int, params: msc_params, x,
+                       info: msc_info | None = None) -> int:
+    """Raw call of the polynomial right-hand-side solve; returns the status."""
+    return load().msc_solve_poly_rhs(ctx, op, _ptr(b), _ptr(sigma), int(S), _ptr(coef), int(deg),
+                                     ctypes.byref(params), _ptr(x),
+                                     ctypes.byref(info) if info is not None else None)
+
+
+def msc_solve_parity(ctx: int, op: int, parity: int, b, nrhs: int, sigma, S: int, params: msc_params, x,
+                     info: msc_info | None = None) -> int:
+    """Raw call of the single-parity solve; returns the status."""
+    return load().msc_solve_parity(ctx, op, int(parity), _ptr(b), int(nrhs), _ptr(sigma), int(S),
+                                   ctypes.byref(params), _ptr(x),
+                                   ctypes.byref(info) if info is not None else None)
+
+
 # ---------------------------------------------------------------------------
 # convenience layer (still only marshalling)
 # ---------------------------------------------------------------------------
@@ -351,6 +390,88 @@ def solve(ctx: int, op: int, b, sigma, x=None, tol=1e-10, precision=MSC_MIXED, m
     if squeeze:
         x = x[0]
     return x, res
+
+
+def solve_parity(ctx: int, op: int, parity: int, b, sigma, x=None, tol=1e-10, precision=MSC_MIXED,
+                 max_iter=100000, reliable_every=50, freeze=True, refine=4, raise_on_error=True):
+    """Shifted family for a source on the sites of one parity (0 even, 1
+    odd) of a staggered operator. `b`: [nrhs][V/2*nc] (or [V/2*nc]) complex128,
+    the parity's sites in site order (site x at index x // 2); `x` (optional)
+    receives [nrhs][S][V/2*nc]. Returns (x, SolveInfo)."""
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    S = int(sig.shape[0])
+    squeeze = False
+    if hasattr(b, "data_ptr"):
+        import torch
+        if b.dim() == 1:
+            b = b.unsqueeze(0)
+            squeeze = True
+        b = b.contiguous()
+        nrhs, n = b.shape
+        if x is None:
+            x = torch.empty((nrhs, S, n), dtype=torch.complex128, device=b.device)
+    else:
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        if b.ndim == 1:
+            b = b[None, :]
+            squeeze = True
+        nrhs, n = b.shape
+        if x is None:
+            x = np.empty((nrhs, S, n), dtype=np.complex128)
+    p = msc_params_default()
+    p.tol, p.max_iter, p.precision = float(tol), int(max_iter), int(precision)
+    p.reliable_every, p.freeze_converged, p.refine = int(reliable_every), int(bool(freeze)), int(refine)
+    it = np.zeros(nrhs * S, dtype=np.int32)
+    rit = np.zeros(nrhs * S, dtype=np.int32)
+    rho = np.zeros(nrhs * S, dtype=np.float64)
+    info = msc_info()
+    info.shift_iters = it.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    info.shift_refine_iters = rit.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    info.true_rel_resid = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = msc_solve_parity(ctx, op, parity, b, nrhs, sig, S, p, x, info)
+    if st != MSC_OK and (raise_on_error and st != MSC_ERR_NOT_CONVERGED):
+        raise MscError(st, "msc_solve_parity")
+    res = SolveInfo(info, it.reshape(nrhs, S), rit.reshape(nrhs, S), rho.reshape(nrhs, S))
+    if squeeze:
+        x = x[0]
+    return x, res
+
+
+def solve_poly_rhs(ctx: int, op: int, b, sigma, coef, x=None, tol=1e-10, precision=MSC_MIXED,
+                   max_iter=100000, reliable_every=50, refine=4, raise_on_error=True):
+    """(A + sigma_s) x_s = q_s(A) b for every shift, q_s(t) = sum_k coef[s][k] t^k.
+    `b`: [n] complex128 (numpy or torch, host or device); `coef`: [S][deg+1]
+    real; `x` (optional) receives [S][n]. Returns (x, SolveInfo); the
+    residuals in the info are relative to |q_s(A) b|."""
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    S = int(sig.shape[0])
+    cf = np.ascontiguousarray(coef, dtype=np.float64).reshape(S, -1)
+    deg = cf.shape[1] - 1
+    if hasattr(b, "data_ptr"):
+        import torch
+        b = b.reshape(-1).contiguous()
+        n = b.shape[0]
+        if x is None:
+            x = torch.empty((S, n), dtype=torch.complex128, device=b.device)
+    else:
+        b = np.ascontiguousarray(b, dtype=np.complex128).reshape(-1)
+        n = b.shape[0]
+        if x is None:
+            x = np.empty((S, n), dtype=np.complex128)
+    p = msc_params_default()
+    p.tol, p.max_iter, p.precision = float(tol), int(max_iter), int(precision)
+    p.reliable_every, p.refine = int(reliable_every), int(refine)
+    it = np.zeros(S, dtype=np.int32)
+    rit = np.zeros(S, dtype=np.int32)
+    rho = np.zeros(S, dtype=np.float64)
+    info = msc_info()
+    info.shift_iters = it.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    info.shift_refine_iters = rit.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    info.true_rel_resid = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = msc_solve_poly_rhs(ctx, op, b, sig, S, cf, deg, p, x, info)
+    if st != MSC_OK and (raise_on_error and st != MSC_ERR_NOT_CONVERGED):
+        raise MscError(st, "msc_solve_poly_rhs")
+    return x, SolveInfo(info, it, rit, rho)
 
 
 def solve_nonherm(ctx: int, op: int, b, sigma, x=None, tol=1e-10, max_iter=100000, freeze=True,

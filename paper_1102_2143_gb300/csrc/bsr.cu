@@ -46,6 +46,60 @@ __global__ void k_bsr_pack(const int64_t* __restrict__ row_ptr, const int32_t* _
     }
 }
 
+// Hermiticity of a block-CSR matrix (repeated columns add): one thread per
+// stored block k = (i, j); for the first block of column j in row i it forms
+// S_ij = sum of row i's blocks in column j and S_ji from row j, and records
+// max |S_ij[a][b] - conj(S_ji[b][a])| in out[0] and max |S_ij[a][b]| in
+// out[1] (non-negative doubles, compared as their bit patterns; a NaN or
+// Inf entry records the largest finite double as the difference). Work per
+// block is the length of its two rows.
+__global__ void k_bsr_herm(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const double2* __restrict__ vals, int64_t nbr, int bd,
+                           unsigned long long* __restrict__ out) {
+    const int64_t nnzb = row_ptr[nbr];
+    double dmax = 0.0, amax = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzb;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        // row i of block k: the last row whose start is <= k
+        int64_t lo = 0, hi = nbr - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (row_ptr[mid] <= k) lo = mid; else hi = mid - 1;
+        }
+        const int64_t i = lo;
+        const int j = col[k];
+        bool first = true;
+        for (int64_t q = row_ptr[i]; q < k; ++q)
+            if (col[q] == j) { first = false; break; }
+        if (!first) continue;
+        double2 sij[9], sji[9];
+        for (int e = 0; e < bd * bd; ++e) sij[e] = sji[e] = {0.0, 0.0};
+        for (int64_t q = k; q < row_ptr[i + 1]; ++q)
+            if (col[q] == j)
+                for (int e = 0; e < bd * bd; ++e) sij[e] = cadd(sij[e], vals[q * bd * bd + e]);
+        for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q)
+            if (col[q] == (int)i)
+                for (int e = 0; e < bd * bd; ++e) sji[e] = cadd(sji[e], vals[q * bd * bd + e]);
+        for (int a = 0; a < bd; ++a)
+            for (int b = 0; b < bd; ++b) {
+                const double2 u = sij[a * bd + b], v = sji[b * bd + a];
+                const double d = fmax(fabs(u.x - v.x), fabs(u.y + v.y));
+                const double m = fmax(fabs(u.x), fabs(u.y));
+                dmax = (d == d && d <= 1.7e308) ? fmax(dmax, d) : 1.7e308;
+                amax = (m == m && m <= 1.7e308) ? fmax(amax, m) : amax;
+            }
+    }
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(dmax));
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(amax));
+}
+
+cudaError_t bsr_check_hermitian(const int64_t* d_row_ptr, const int32_t* d_col, const double2* d_vals,
+                                int64_t nbr, int bd, unsigned long long* d_out, cudaStream_t st) {
+    k_bsr_herm<<<resident_grid((const void*)k_bsr_herm, std::max<int64_t>(nbr * 8, 1)), kThreads, 0, st>>>(
+        d_row_ptr, d_col, d_vals, nbr, bd, d_out);
+    return cudaGetLastError();
+}
+
 cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
                      const double2* d_vals, int* d_bad, cudaStream_t st) {
     int64_t rows = op.nslices * 32;

@@ -77,6 +77,7 @@ struct msc_ctx {
     Buf actb;         // {count, indices} of the systems still iterating (refinement)
     Buf bcg;          // BiCGStab-M scalars: one BcgSys, then S BcgSlot
     Buf condf;        // one flag per iteration of a chunk graph (conditional update bodies)
+    Buf pb, px0, ptmp;// polynomial right-hand sides: b_s, x_s0, two scratch vectors per shift
     int use_cond = 1; // build reliable updates as conditional graph nodes
     int* h_flags = nullptr;  // pinned copy of the conditional flags of a chunk
     int* h_act = nullptr;
@@ -98,6 +99,10 @@ struct msc_op {
     long uid = 0;
     OpDev dev{};
     int64_t nnzb = 0;
+    // staggered: the parity-reduced operators of sources on even (0) or odd
+    // (1) sites, made on first use; they share this operator's device data
+    msc_op* view[2] = {nullptr, nullptr};
+    bool is_view = false;
 };
 
 #define CK(call)                                      \
@@ -202,8 +207,13 @@ static Engine engine_of(msc_ctx* c) {
     return e;
 }
 
-static VecSet vecs_of(msc_ctx* c, int prec, int64_t npad) {
+// FP32 vectors of a staggered operator are colour-planar (see VecSet).
+static VecSet vecs_of(msc_ctx* c, int prec, int64_t npad, const OpDev& A) {
     VecSet v;
+    if (A.kind == OP_STAGGERED && prec == PREC_F32) {
+        v.pl_nc = A.nc;
+        v.pl_V = vlen(A.g);
+    }
     v.r = c->r.p;
     v.p = c->p.p;
     v.t = c->t.p;
@@ -244,8 +254,11 @@ static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int o
                            bool per_system = false) {
     Engine e = eng ? *eng : engine_of(c);
     c->launches++;
-    if (A.kind == OP_STAGGERED)
+    if (A.kind == OP_STAGGERED) {
+        if (!per_system && stag_group_applies(A, prec, kind, npass))
+            return launch_stag_group(A, kind, e, dsec(c, sec), npass, c->work, act);
         return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work, act, per_system);
+    }
     return launch_bsr_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work, act, per_system,
                            npass == 1 ? hsec(c, sec) : nullptr);
 }
@@ -258,7 +271,7 @@ static cudaError_t enqueue_chunk(msc_ctx* c, const OpDev& A, int prec, int nsys,
                                  bool reliable, bool profile, int64_t npad, int group, int groups,
                                  int& kernels) {
     Engine e = engine_of(c);
-    VecSet v = vecs_of(c, prec, npad);
+    VecSet v = vecs_of(c, prec, npad, A);
     const int* act = (const int*)c->actb.p;
     kernels = 0;
     for (int it = 0; it < chunk; ++it) {
@@ -329,7 +342,7 @@ static cudaError_t build_chunk_graph_cond(msc_ctx* c, const OpDev& A, int prec, 
     cudaGraph_t g = nullptr;
     err = cudaGraphCreate(&g, 0);
     if (err != cudaSuccess) return err;
-    VecSet v = vecs_of(c, prec, npad);
+    VecSet v = vecs_of(c, prec, npad, A);
     std::vector<cudaGraphNode_t> tail;
     kernels = 0;
     for (int it = 0; it < chunk && err == cudaSuccess; ++it) {
@@ -449,6 +462,7 @@ static int get_graph(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
 
 struct ProfAcc {
     double k1 = 0, k2 = 0, k3 = 0;
+    double act = 0;  // non-base shifts still iterating at the sampled iterations (summed)
     int n = 0;
 };
 
@@ -481,6 +495,23 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
     }
     CK(cudaMemcpyAsync(c->h_sys, c->sys.p, sizeof(SysScalars) * nsys, cudaMemcpyDeviceToHost, c->work));
     CK(cudaStreamSynchronize(c->work));
+    // profiled stages: the non-base shifts still iterating when a chunk
+    // starts (the shifts its first, sampled, update kernel moves)
+    const bool track = profile && pa;
+    int nslot_all = 0;
+    for (int j = 0; j < nsys; ++j) nslot_all = std::max(nslot_all, c->h_sys[j].slot0 + c->h_sys[j].S);
+    auto count_active = [&]() {
+        int a = 0;
+        for (int j = 0; j < nsys; ++j)
+            for (int k = 0; k < c->h_sys[j].S; ++k)
+                if (k != c->h_sys[j].base && c->h_slot[c->h_sys[j].slot0 + k].active) ++a;
+        return a;
+    };
+    if (track) {
+        CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslot_all, cudaMemcpyDeviceToHost, c->work));
+        CK(cudaStreamSynchronize(c->work));
+    }
+    int act_now = track ? count_active() : 0;
     // max_iter = 0 runs no iteration (the device sees the cap only after one)
     const long max_chunks = max_iter > 0 ? (long)max_iter / chunk + 2 : 0;
     for (long k = 0; k < max_chunks; ++k) {
@@ -506,9 +537,12 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
                            c->work));
         const int ncf = std::min(ge->cond_chunk, 1024);
         if (ncf) CK(cudaMemcpyAsync(c->h_flags, c->condf.p, sizeof(int) * ncf, cudaMemcpyDeviceToHost, c->work));
+        if (track)
+            CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslot_all, cudaMemcpyDeviceToHost,
+                               c->work));
         CK(cudaStreamSynchronize(c->work));
         for (int i = 0; i < ncf; ++i) c->launches += c->h_flags[i] ? ge->cond_kernels : 0;
-        if (profile && pa && all_running) {
+        if (track && all_running) {
             float a = 0, b = 0, d = 0;
             if (cudaEventElapsedTime(&a, c->prof[0], c->prof[1]) == cudaSuccess &&
                 cudaEventElapsedTime(&b, c->prof[1], c->prof[2]) == cudaSuccess &&
@@ -516,9 +550,11 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
                 pa->k1 += a;
                 pa->k2 += b;
                 pa->k3 += d;
+                pa->act += act_now;
                 pa->n++;
             }
         }
+        if (track) act_now = count_active();
     }
     if (rel_updates)
         for (int j = 0; j < nsys; ++j) *rel_updates += c->h_sys[j].nru;
@@ -626,7 +662,8 @@ int msc_destroy(msc_ctx* c) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     Buf* bufs[] = {&c->sys, &c->slot, &c->partial, &c->counter, &c->out_red, &c->descs,
                    &c->b64, &c->x64, &c->t64, &c->r, &c->p, &c->t, &c->ps, &c->xit,
-                   &c->coef, &c->force, &c->btab, &c->actb, &c->condf, &c->bcg};
+                   &c->coef, &c->force, &c->btab, &c->actb, &c->condf, &c->bcg,
+                   &c->pb, &c->px0, &c->ptmp};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_sys) cudaFreeHost(c->h_sys);
@@ -650,23 +687,31 @@ static void free_op_dev(OpDev& d) {
     memset(&d, 0, sizeof d);
 }
 
-int msc_op_destroy(msc_op* op) {
-    if (!op) return MSC_ERR_ARG;
-    if (msc_ctx* c = op->ctx) {
-        cudaSetDevice(c->device);
-        // the context's graphs of this operator ("<uid>|..." and "bcg|<uid>|...")
-        // go with it, after the work stream has drained
-        if (c->work) cudaStreamSynchronize(c->work);
-        const std::string a = std::to_string(op->uid) + "|", b = "bcg|" + a;
-        for (auto it = c->graphs.begin(); it != c->graphs.end();) {
-            if (it->first.compare(0, a.size(), a) == 0 || it->first.compare(0, b.size(), b) == 0) {
-                if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
-                it = c->graphs.erase(it);
-            } else {
-                ++it;
-            }
+// Drops the context's graphs of operator uid ("<uid>|..." and "bcg|<uid>|...").
+static void drop_graphs(msc_ctx* c, long uid) {
+    const std::string a = std::to_string(uid) + "|", b = "bcg|" + a;
+    for (auto it = c->graphs.begin(); it != c->graphs.end();) {
+        if (it->first.compare(0, a.size(), a) == 0 || it->first.compare(0, b.size(), b) == 0) {
+            if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+            it = c->graphs.erase(it);
+        } else {
+            ++it;
         }
     }
+}
+
+int msc_op_destroy(msc_op* op) {
+    if (!op || op->is_view) return MSC_ERR_ARG;
+    if (msc_ctx* c = op->ctx) {
+        cudaSetDevice(c->device);
+        // the context's graphs of this operator and of its parity views go
+        // with it, after the work stream has drained
+        if (c->work) cudaStreamSynchronize(c->work);
+        drop_graphs(c, op->uid);
+        for (msc_op* v : op->view)
+            if (v) drop_graphs(c, v->uid);
+    }
+    for (msc_op* v : op->view) delete v;
     free_op_dev(op->dev);
     delete op;
     return MSC_OK;
@@ -742,10 +787,15 @@ int msc_op_staggered(msc_ctx* c, msc_op** out, int nc, const int dims[4], const 
     return MSC_OK;
 }
 
+// MSC_CHECK_HERMITIAN: entries may differ from the conjugate of their
+// transposed partner by this much relative to the largest entry (rounding of
+// a matrix assembled in FP64 by different paths for (i, j) and (j, i)).
+constexpr double kHermitianTol = 1e-12;
+
 int msc_op_bsr(msc_ctx* c, msc_op** out, int64_t nbr, int bd, const int64_t* row_ptr,
                const int32_t* col_idx, const double* vals, unsigned flags) {
-    (void)flags;
     if (!c || !out || !row_ptr || !col_idx || !vals) return MSC_ERR_ARG;
+    if (flags & ~MSC_CHECK_HERMITIAN) return MSC_ERR_ARG;
     *out = nullptr;
     if (bd < 1 || bd > 3 || nbr <= 0 || nbr > ((int64_t)1 << 31) - 1) return MSC_ERR_ARG;
     int st = begin(c);
@@ -787,11 +837,13 @@ int msc_op_bsr(msc_ctx* c, msc_op** out, int64_t nbr, int bd, const int64_t* row
     d.nslots_blk = acc;
     void *trp = nullptr, *tcol = nullptr, *tval = nullptr;
     int* dbad = nullptr;
+    unsigned long long* dherm = nullptr;
     auto fail = [&](int code) {
         if (trp) cudaFree(trp);
         if (tcol) cudaFree(tcol);
         if (tval) cudaFree(tval);
         if (dbad) cudaFree(dbad);
+        if (dherm) cudaFree(dherm);
         free_op_dev(d);
         delete op;
         return code;
@@ -827,6 +879,19 @@ int msc_op_bsr(msc_ctx* c, msc_op** out, int64_t nbr, int bd, const int64_t* row
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
     if (e != cudaSuccess) return fail(cuda_status(e));
     if (bad) return fail(MSC_ERR_ARG);
+    if (flags & MSC_CHECK_HERMITIAN) {
+        // the columns are known to be in range now (the packing checked them)
+        double hm[2] = {0.0, 0.0};
+        e = cudaMalloc((void**)&dherm, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(dherm, 0, 2 * sizeof(unsigned long long), c->work);
+        if (e == cudaSuccess) e = bsr_check_hermitian((const int64_t*)trp, dcol, dval, nbr, bd, dherm, c->work);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hm, dherm, sizeof hm, cudaMemcpyDeviceToHost, c->work);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+        if (!(hm[0] <= kHermitianTol * hm[1])) return fail(MSC_ERR_NOT_HPD);
+        cudaFree(dherm);
+        dherm = nullptr;
+    }
     cudaFree(trp);
     if (tcol) cudaFree(tcol);
     if (tval) cudaFree(tval);
@@ -921,7 +986,8 @@ static int apply_impl(msc_ctx* c, const msc_op* op, double sigma, const double* 
         float2* in32 = (float2*)c->r.p;
         float2* mid32 = (float2*)c->t.p;
         float2* out32 = (float2*)c->p.p;
-        CK(launch_convert(in64, 0, in32, 1, n, c->work));
+        if (A.kind == OP_STAGGERED) CK(launch_convert_planar(in64, in32, A.nc, A.g.V, true, c->work));
+        else CK(launch_convert(in64, 0, in32, 1, n, c->work));
         if (A.kind == OP_STAGGERED) {
             hsec(c, D_AP1)[0] = mkdesc(in32, nullptr, nullptr, mid32, 0.0, -1, -1, FIN_NONE);
             hsec(c, D_AP2)[0] = mkdesc(mid32, in32, nullptr, out32, dstag + sigma, -1, -1, FIN_NONE);
@@ -934,7 +1000,8 @@ static int apply_impl(msc_ctx* c, const msc_op* op, double sigma, const double* 
             CK(upload_sec(c, D_AP2, 1));
             CK(op_pass(c, A, PREC_F32, PASS_D, 0, D_AP2, 1));
         }
-        CK(launch_convert(out32, 1, out64, 0, n, c->work));
+        if (A.kind == OP_STAGGERED) CK(launch_convert_planar(out32, out64, A.nc, A.g.V, false, c->work));
+        else CK(launch_convert(out32, 1, out64, 0, n, c->work));
     }
     CK(cudaMemcpyAsync(out, out64, n * 16, cudaMemcpyDefault, c->work));
     CK(cudaStreamSynchronize(c->work));
@@ -950,11 +1017,105 @@ int msc_op_dslash(msc_ctx* c, const msc_op* op, const double* in, double* out) {
     return apply_impl(c, op, 0.0, in, out, MSC_FP64, true);
 }
 
-int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const double* sigma, int S,
-              const msc_params* prm_in, double* x, msc_info* info) {
+}  // extern "C"
+
+// Right-hand sides of polynomial form, b_s = q_s(A) b (Sec. 5, eq. linprobgen):
+// q_s(t) = sum_k coef[s * (deg + 1) + k] t^k.
+struct PolyRhs {
+    const double* coef;
+    int deg;
+};
+
+// b_s = q_s(A) b into c->pb and x_s0 = s_s(A) b into c->px0 for every shift,
+// where q_s(t) = q_s(-sigma_s) + (t + sigma_s) s_s(t) (synthetic division by
+// t + sigma_s); cs[s] = q_s(-sigma_s), bs2[s] = |b_s|^2, b2 = |b|^2. Horner's
+// rule on the device with the FP64 operator, every shift in one launch per
+// step.
+static int poly_setup(msc_ctx* c, const OpDev& A, const double2* b, int64_t n, int64_t npad,
+                      const double* sigma, int S, const PolyRhs& pr, std::vector<double>& cs,
+                      std::vector<double>& bs2, double& b2) {
+    const int d = pr.deg;
+    std::vector<double> sco((size_t)S * std::max(d, 1), 0.0);  // s_s: [S][d], constant term first
+    for (int s = 0; s < S; ++s) {
+        const double* a = pr.coef + (size_t)s * (d + 1);
+        const double r = -sigma[s];
+        if (d == 0) {
+            cs[s] = a[0];
+            continue;
+        }
+        double* q = sco.data() + (size_t)s * d;
+        q[d - 1] = a[d];
+        for (int k = d - 1; k >= 1; --k) q[k - 1] = a[k] + r * q[k];
+        cs[s] = a[0] + r * q[0];
+    }
+    bool moved = false;
+    const size_t vb = (size_t)S * npad * 16;
+    CK(grow(c, c->pb, vb, moved));
+    CK(grow(c, c->px0, vb, moved));
+    CK(grow(c, c->ptmp, 2 * vb, moved));
+    if (moved) c->gen++;
+    double2* pb = (double2*)c->pb.p;
+    double2* px0 = (double2*)c->px0.p;
+    double2* mid = (double2*)c->ptmp.p;
+    double2* out = mid + (size_t)S * npad;
+    const double dstag = A.kind == OP_STAGGERED ? A.mass * A.mass : 0.0;
+    // v_s <- sum_k co[s][k] A^k b, co given constant term first, `deg` + 1 terms
+    auto horner = [&](double2* v, int deg, auto coef_of) -> int {
+        ShiftCoef a{};
+        for (int s = 0; s < S; ++s) a.v[s] = coef_of(s, deg);
+        CK(launch_poly_step(v, nullptr, a, b, S, n, npad, c->work));
+        c->launches++;
+        if (deg == 0) return MSC_OK;
+        // descriptors of out_s = A v_s for every shift (FP64)
+        CK(cudaStreamSynchronize(c->work));
+        for (int s = 0; s < S; ++s) {
+            double2* vs = v + (size_t)s * npad;
+            if (A.kind == OP_STAGGERED) {
+                hsec(c, D_AP1)[s] = mkdesc(vs, nullptr, nullptr, mid + (size_t)s * npad, 0.0, -1, -1, FIN_NONE);
+                hsec(c, D_AP2)[s] = mkdesc(mid + (size_t)s * npad, vs, nullptr, out + (size_t)s * npad, dstag, -1, -1,
+                                           FIN_NONE);
+            } else {
+                hsec(c, D_AP2)[s] = mkdesc(vs, vs, nullptr, out + (size_t)s * npad, 0.0, -1, -1, FIN_NONE);
+            }
+        }
+        CK(upload_sec(c, D_AP1, S));
+        CK(upload_sec(c, D_AP2, S));
+        for (int k = deg - 1; k >= 0; --k) {
+            if (A.kind == OP_STAGGERED) CK(op_pass(c, A, PREC_F64, PASS_A, 0, D_AP1, S));
+            CK(op_pass(c, A, PREC_F64, PASS_D, 0, D_AP2, S));
+            for (int s = 0; s < S; ++s) a.v[s] = coef_of(s, k);
+            CK(launch_poly_step(v, out, a, b, S, n, npad, c->work));
+            c->launches++;
+        }
+        CK(cudaStreamSynchronize(c->work));
+        return MSC_OK;
+    };
+    int st = horner(pb, d, [&](int s, int k) { return pr.coef[(size_t)s * (d + 1) + k]; });
+    if (st) return st;
+    if (d >= 1) st = horner(px0, d - 1, [&](int s, int k) { return sco[(size_t)s * d + k]; });
+    else CK(cudaMemsetAsync(px0, 0, vb, c->work));
+    if (st) return st;
+    // |b_s|^2 (rows 0 .. S-1) and |b|^2 (row S)
+    CK(cudaMemcpyAsync(mid, b, n * 16, cudaMemcpyDeviceToDevice, c->work));
+    Engine e = engine_of(c);
+    CK(launch_norms(e, pb, S, n, npad, c->work));
+    CK(cudaMemcpyAsync(c->h_red, c->out_red.p, sizeof(double) * S, cudaMemcpyDeviceToHost, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    for (int s = 0; s < S; ++s) bs2[s] = c->h_red[s];
+    CK(launch_norms(e, mid, 1, n, npad, c->work));
+    CK(cudaMemcpyAsync(c->h_red, c->out_red.p, sizeof(double), cudaMemcpyDeviceToHost, c->work));
+    CK(cudaStreamSynchronize(c->work));
+    b2 = c->h_red[0];
+    c->launches += 2;
+    return MSC_OK;
+}
+
+static int solve_impl(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const double* sigma, int S,
+                      const msc_params* prm_in, double* x, msc_info* info, const PolyRhs* poly) {
     const auto t0 = std::chrono::steady_clock::now();
-    const Range whole("msc_solve");
+    const Range whole(poly ? "msc_solve_poly_rhs" : "msc_solve");
     if (!c || !op || !b || !x || !sigma || nrhs <= 0 || S <= 0 || S > kMaxShifts) return MSC_ERR_ARG;
+    if (poly && nrhs != 1) return MSC_ERR_ARG;
     msc_params prm;
     msc_params_default(&prm);
     if (prm_in) prm = *prm_in;
@@ -971,7 +1132,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     const OpDev& A = op->dev;
     const int64_t n = A.n, npad = (n + 63) / 64 * 64;
     const int nslots = nrhs * S;
-    const int rows = std::max(nrhs, nslots);
+    const int rows = std::max(nrhs, nslots) + (poly ? 1 : 0);
     st = ensure_ws(c, npad, rows, nslots, nrhs, mixed ? 8 : 16);
     if (st) return st;
     const long launches0 = c->launches;
@@ -989,6 +1150,23 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         CK(cudaMemset2DAsync(r + n * elem, npad * elem, 0, (npad - n) * elem, rows, c->work));
     }
     CK(cudaMemcpy2DAsync(b64, npad * 16, b, n * 16, n * 16, nrhs, cudaMemcpyDefault, c->work));
+    // right-hand side of each slot for the checks and refinement (b of its
+    // right-hand side, or b_s = q_s(A) b) and |.|^2 of it
+    std::vector<const double2*> src_of(nslots);
+    std::vector<double> bn2_of(nslots, -1.0);
+    for (int g = 0; g < nslots; ++g) src_of[g] = b64 + (size_t)(g / S) * npad;
+    // polynomial right-hand sides: x_s = x_s0 + c_s z_s with z_s = (A+sigma_s)^-1 b
+    std::vector<double> pcs(S, 1.0), pbs2(S, 0.0);
+    double pb2 = 0.0;
+    if (poly) {
+        const Range pr("msc_solve_poly_rhs: b_s and initial guesses");
+        st = poly_setup(c, A, b64, n, npad, sigma, S, *poly, pcs, pbs2, pb2);
+        if (st) return st;
+        for (int s = 0; s < S; ++s) {
+            src_of[s] = (const double2*)c->pb.p + (size_t)s * npad;
+            bn2_of[s] = pbs2[s];
+        }
+    }
     // ---- multi-shift stage ------------------------------------------------
     int base = 0;
     for (int s = 1; s < S; ++s)
@@ -998,7 +1176,20 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     const double d0 = dstag + sigma0;
     for (int j = 0; j < nrhs; ++j) {
         init_sys(c->h_sys[j], S, base, j * S, j, d0, prm.tol, prm.max_iter, prm.freeze_converged, prm);
-        for (int s = 0; s < S; ++s) init_slot(c->h_slot[j * S + s], sigma[s] - sigma0);
+        for (int s = 0; s < S; ++s) {
+            SlotScalars& q = c->h_slot[j * S + s];
+            init_slot(q, sigma[s] - sigma0);
+            if (poly) {
+                // z_s needs |r_s| <= tol |b_s| / |c_s|; a shift with c_s = 0 or
+                // b_s = 0 needs no z_s at all
+                if (pcs[s] == 0.0 || !(pbs2[s] > 0.0) || !(pb2 > 0.0)) {
+                    q.active = 0;
+                    q.conv_iter = 0;
+                } else {
+                    q.tol2 = prm.tol * prm.tol * pbs2[s] / (pcs[s] * pcs[s] * pb2);
+                }
+            }
+        }
         const double2* bj = b64 + (size_t)j * npad;
         double2* xb = x64 + (size_t)(j * S + base) * npad;
         void* rj = r + (size_t)j * npad * elem;
@@ -1021,7 +1212,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     CK(cudaMemcpyAsync(c->slot.p, c->h_slot, sizeof(SlotScalars) * nslots, cudaMemcpyHostToDevice, c->work));
     for (int s : {D_INIT, D_K1, D_K2, D_RUA, D_RUC}) CK(upload_sec(c, s, nrhs));
     Engine e = engine_of(c);
-    VecSet v = vecs_of(c, prec, npad);
+    VecSet v = vecs_of(c, prec, npad, A);
     CK(launch_init(prec, e, v, dsec(c, D_INIT), nrhs, c->work));
     c->launches++;
     const int chunk = 25;
@@ -1046,10 +1237,21 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         CK(launch_fold(e, v, nrhs, 0, c->work));
         c->launches++;
     }
+    if (poly && status == MSC_OK) {
+        // x_s = c_s z_s + x_s0 (x_s = 0 where b_s = 0)
+        ShiftCoef cf{};
+        for (int s = 0; s < S; ++s) cf.v[s] = pbs2[s] > 0.0 ? pcs[s] : 0.0;
+        CK(launch_poly_combine(x64, (const double2*)c->px0.p, cf, S, n, npad, c->work));
+        for (int s = 0; s < S; ++s)
+            if (!(pbs2[s] > 0.0)) CK(cudaMemsetAsync(x64 + (size_t)s * npad, 0, npad * 16, c->work));
+        c->launches++;
+    }
     CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslots, cudaMemcpyDeviceToHost, c->work));
     CK(cudaStreamSynchronize(c->work));
     std::vector<int> shift_iters(nslots), ref_iters(nslots, 0);
     for (int g = 0; g < nslots; ++g) shift_iters[g] = c->h_slot[g].conv_iter;
+    for (int g = 0; g < nslots; ++g)
+        if (bn2_of[g] < 0.0) bn2_of[g] = bnorm2[g / S];
     // ---- true residuals and refinement -----------------------------------
     // Round r computes, for every shift still to check, the FP64 true residual
     // b - (A + sigma_s) x_s; that residual is also the start of the shift's
@@ -1059,8 +1261,11 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
     std::vector<double> rho(nslots, std::nan(""));
     int rounds = 0, ref_total = 0;
     if (status == MSC_OK) {
-        std::vector<int> todo(nslots);
-        for (int g = 0; g < nslots; ++g) todo[g] = g;
+        std::vector<int> todo;
+        for (int g = 0; g < nslots; ++g) {
+            if (bn2_of[g] > 0.0) todo.push_back(g);
+            else rho[g] = 0.0;  // b_s = 0: x_s = 0 exactly
+        }
         for (int round = 0; !todo.empty(); ++round) {
             const Range rr("msc_solve: FP64 check and refinement round");
             const bool check_only = round >= prm.refine;
@@ -1080,9 +1285,9 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
                 // iteration drifts off and ends non-finite)
                 c->h_sys[k].ru_every = 4 * prm.reliable_every;
                 c->h_sys[k].delta2 = 0.01 * prm.reliable_delta * prm.reliable_delta;
-                c->h_sys[k].bnorm2 = bnorm2[rhs];
+                c->h_sys[k].bnorm2 = bn2_of[g];
                 init_slot(c->h_slot[g], 0.0);
-                const double2* bj = b64 + (size_t)rhs * npad;
+                const double2* bj = src_of[g];
                 double2* xg = x64 + (size_t)g * npad;
                 void* rk = r + (size_t)k * npad * elem;
                 void* pk = p + (size_t)k * npad * elem;
@@ -1113,7 +1318,7 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
             for (int k = 0; k < m; ++k) {
                 const SysScalars& s = c->h_sys[k];
                 const int g = todo[k];
-                const double bn2 = bnorm2[g / S];
+                const double bn2 = bn2_of[g];
                 rho[g] = bn2 > 0 ? std::sqrt(s.R / bn2) : 0.0;
                 if (s.status == ST_ERR_NONFINITE) status = MSC_ERR_NONFINITE;
                 else if (s.status == ST_RUNNING) next.push_back(g);
@@ -1166,8 +1371,43 @@ int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const dou
         info->rupdate_ms = pa.n ? pa.k2 / pa.n : 0.0;
         info->update_ms = pa.n ? pa.k3 / pa.n : 0.0;
         info->prof_samples = pa.n;
+        info->prof_active = pa.n ? pa.act / pa.n : 0.0;
     }
     return status;
+}
+
+extern "C" {
+
+int msc_solve(msc_ctx* c, const msc_op* op, const double* b, int nrhs, const double* sigma, int S,
+              const msc_params* prm, double* x, msc_info* info) {
+    return solve_impl(c, op, b, nrhs, sigma, S, prm, x, info, nullptr);
+}
+
+int msc_solve_poly_rhs(msc_ctx* c, const msc_op* op, const double* b, const double* sigma, int S,
+                       const double* coef, int deg, const msc_params* prm, double* x, msc_info* info) {
+    if (!coef || deg < 0 || deg > MSC_MAX_POLY_DEGREE || S <= 0 || S > kMaxShifts) return MSC_ERR_ARG;
+    for (int64_t k = 0; k < (int64_t)S * (deg + 1); ++k)
+        if (!std::isfinite(coef[k])) return MSC_ERR_ARG;
+    const PolyRhs pr{coef, deg};
+    return solve_impl(c, op, b, 1, sigma, S, prm, x, info, &pr);
+}
+
+int msc_solve_parity(msc_ctx* c, const msc_op* op, int parity, const double* b, int nrhs, const double* sigma,
+                     int S, const msc_params* prm, double* x, msc_info* info) {
+    if (!c || !op || op->is_view || op->dev.kind != OP_STAGGERED || (parity != 0 && parity != 1))
+        return MSC_ERR_ARG;
+    msc_op* self = const_cast<msc_op*>(op);
+    if (!self->view[parity]) {
+        msc_op* v = new msc_op();
+        v->ctx = op->ctx;
+        v->uid = ++g_op_uid;
+        v->dev = op->dev;
+        v->dev.g.eo = 1 + parity;
+        v->dev.n = (int64_t)(op->dev.g.V / 2) * op->dev.nc;
+        v->is_view = true;
+        self->view[parity] = v;
+    }
+    return solve_impl(c, self->view[parity], b, nrhs, sigma, S, prm, x, info, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1317,6 +1557,7 @@ int msc_solve_nonherm(msc_ctx* c, const msc_op* op, const double* b, int nrhs, c
         }
         info->op_ms = info->rupdate_ms = info->update_ms = 0.0;
         info->prof_samples = 0;
+        info->prof_active = 0.0;
     }
     return status;
 }
@@ -2008,6 +2249,7 @@ extern "C" int msc_solve_batched(msc_ctx* c, int nprob, const msc_problem* probs
             }
             in->op_ms = in->rupdate_ms = in->update_ms = 0.0;
             in->prof_samples = 0;
+            in->prof_active = 0.0;
         }
         if (pst != MSC_OK && (worst == MSC_OK || worst == MSC_ERR_NOT_CONVERGED)) worst = pst;
         gfirst += q.nrhs * q.S;
@@ -2108,6 +2350,9 @@ namespace {
 
 constexpr int64_t kNoallocMaxN = (int64_t)1 << 20;  // complex unknowns (16 MiB of FP64)
 constexpr size_t kNoallocDescBytes = 256;
+// the two pass descriptors sit in front of the D x vector
+static_assert(2 * sizeof(PassDesc) <= kNoallocDescBytes && kNoallocDescBytes % 16 == 0,
+              "the descriptor area of the scratch array must hold two 16-byte aligned PassDesc");
 // Held by every device that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocDescBytes + 16 * kNoallocMaxN];
 
@@ -2120,6 +2365,19 @@ __global__ void k_noalloc_store_descs(PassDesc* dst, PassDesc a, PassDesc b) {
         dst[0] = a;
         dst[1] = b;
     }
+}
+
+// True when p is memory the kernels on device `dev` may dereference directly:
+// device memory of that device, or managed memory. Device memory of another
+// GPU is refused (without peer access its use would fault on the device).
+bool usable_on_device(const void* p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -2148,7 +2406,7 @@ extern "C" int msc_op_apply_noalloc(const msc_op* op, double sigma, const double
         }
         base = g_noalloc_ptr[dev];
     }
-    if (status == MSC_OK && (!is_device_ptr(in) || !is_device_ptr(out))) status = MSC_ERR_ARG;
+    if (status == MSC_OK && (!usable_on_device(in, dev) || !usable_on_device(out, dev))) status = MSC_ERR_ARG;
     if (status == MSC_OK) {
         cudaStream_t st = (cudaStream_t)stream;
         PassDesc* descs = (PassDesc*)base;

@@ -60,6 +60,55 @@ __global__ void __launch_bounds__(kThreads) k_init(Engine e, VecSet v, const Pas
     if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize(e, d, tot);
 }
 
+// k_init for colour-planar FP32 vectors (staggered operators, see VecSet):
+// one thread per site and colour plane index, reading the site's FP64 source
+// contiguously and writing each FP32 vector's planes coalesced; the pad
+// entries [n, npad) of the FP32 vectors are zeroed.
+template <int NC>
+__global__ void __launch_bounds__(kThreads) k_init_pl(Engine e, VecSet v, const PassDesc* descs, int nsys) {
+    const SysBlock q = sys_block(nsys, nullptr);
+    if (!q.ok) return;
+    const PassDesc d = descs[q.j];
+    const int j = d.sys;
+    const SysScalars* s = &e.sys[j];
+    const int S = s->S, base = s->base, slot0 = s->slot0, rhs = s->rhs;
+    const int V = v.pl_V;
+    const int64_t npad = v.npad, n = (int64_t)V * NC;
+    float2* r = (float2*)v.r + (size_t)j * npad;
+    float2* p = (float2*)v.p + (size_t)j * npad;
+    float2* ps = (float2*)v.ps;
+    float2* xit = (float2*)v.xit;
+    const double2* b = v.b64 + (size_t)rhs * npad;
+    double local = 0.0;
+    const int64_t step = (int64_t)q.gx * blockDim.x;
+    for (int64_t x = q.bx * (int64_t)blockDim.x + threadIdx.x; x < V; x += step) {
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            const double2 bv = b[x * NC + a];
+            local += sq(bv);
+            const float2 f = make_float2((float)bv.x, (float)bv.y);
+            const size_t i = (size_t)a * V + x;
+            r[i] = f;
+            p[i] = f;
+            for (int k = 0; k < S; ++k) {
+                const size_t g = (size_t)(slot0 + k) * npad + i;
+                if (k != base) ps[g] = f;
+                xit[g] = make_float2(0.f, 0.f);
+                v.x64[(size_t)(slot0 + k) * npad + x * NC + a] = {0.0, 0.0};
+            }
+        }
+    }
+    for (int64_t i = n + q.bx * (int64_t)blockDim.x + threadIdx.x; i < npad; i += step) {
+        r[i] = p[i] = make_float2(0.f, 0.f);
+        for (int k = 0; k < S; ++k) {
+            const size_t g = (size_t)(slot0 + k) * npad + i;
+            ps[g] = xit[g] = make_float2(0.f, 0.f);
+        }
+    }
+    double tot;
+    if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize(e, d, tot);
+}
+
 // p = r, p_s = r, x accumulator of the system's shifts = 0 (start of a solve
 // whose residual r was just computed from a warm start).
 template <class T>
@@ -246,6 +295,52 @@ __global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v, int only_
     }
 }
 
+// k_fold for colour-planar FP32 accumulators: one thread per site, the
+// site's FP64 entries of each shift read and written contiguously.
+template <int NC>
+__global__ void __launch_bounds__(kThreads) k_fold_pl(Engine e, VecSet v, int only_ru, int nsys, const int* act) {
+    const SysBlock sb = sys_block(nsys, act);
+    if (!sb.ok) return;
+    const int j = sb.j;
+    const SysScalars* s = &e.sys[j];
+    const int st = load_status(s);
+    if (st == ST_ERR_NOT_HPD || st == ST_ERR_NONFINITE) return;
+    if (only_ru && (st != ST_RUNNING || __ldcg(&s->ru) == 0)) return;
+    const int S = s->S, slot0 = s->slot0;
+    const int V = v.pl_V;
+    float2* xa = (float2*)v.xit;
+    for (int64_t x = sb.bx * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)sb.gx * blockDim.x) {
+        for (int k = 0; k < S; ++k) {
+            const size_t g = (size_t)(slot0 + k) * v.npad;
+            double2* xs = v.x64 + g + x * NC;
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                float2* dp = xa + g + (size_t)a * V + x;
+                const float2 dx = *dp;
+                double2 xv = xs[a];
+                xv.x += dx.x;
+                xv.y += dx.y;
+                xs[a] = xv;
+                *dp = make_float2(0.f, 0.f);
+            }
+        }
+    }
+}
+
+__global__ void k_convert_pl(const void* src, void* dst, int nc, int V, int to_planar) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < nc; ++a) {
+            const size_t sm = (size_t)x * nc + a, pl = (size_t)a * V + x;
+            if (to_planar) {
+                const double2 u = ((const double2*)src)[sm];
+                ((float2*)dst)[pl] = make_float2((float)u.x, (float)u.y);
+            } else {
+                const float2 u = ((const float2*)src)[pl];
+                ((double2*)dst)[sm] = make_double2(u.x, u.y);
+            }
+        }
+}
+
 __global__ void k_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -255,6 +350,76 @@ __global__ void k_convert(const void* src, int src_f32, void* dst, int dst_f32, 
         if (dst_f32) ((float2*)dst)[i] = make_float2((float)v.x, (float)v.y);
         else ((double2*)dst)[i] = v;
     }
+}
+
+// ---------------------------------------------------------------------------
+// right-hand sides of polynomial form (FP64, one launch for all shifts):
+// blockIdx.y = shift s, vectors [s][npad] site-major
+// ---------------------------------------------------------------------------
+
+// v_s = Av_s + a_s b (Av = null: v_s = a_s b), one Horner step of every shift
+__global__ void k_poly_step(double2* __restrict__ v, const double2* __restrict__ Av, ShiftCoef a,
+                            const double2* __restrict__ b, int64_t n, int64_t npad) {
+    const int s = blockIdx.y;
+    const double as = a.v[s];
+    double2* vs = v + (size_t)s * npad;
+    const double2* As = Av ? Av + (size_t)s * npad : nullptr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 bi = b[i];
+        double2 o = As ? As[i] : make_double2(0.0, 0.0);
+        o.x = fma(as, bi.x, o.x);
+        o.y = fma(as, bi.y, o.y);
+        vs[i] = o;
+    }
+}
+
+// x_s = c_s x_s + x0_s (x0 = null: x_s = c_s x_s)
+__global__ void k_poly_combine(double2* __restrict__ x, const double2* __restrict__ x0, ShiftCoef c, int64_t n,
+                               int64_t npad) {
+    const int s = blockIdx.y;
+    const double cs = c.v[s];
+    double2* xs = x + (size_t)s * npad;
+    const double2* x0s = x0 ? x0 + (size_t)s * npad : nullptr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 o = x0s ? x0s[i] : make_double2(0.0, 0.0);
+        const double2 xi = xs[i];
+        o.x = fma(cs, xi.x, o.x);
+        o.y = fma(cs, xi.y, o.y);
+        xs[i] = o;
+    }
+}
+
+// out_red[s] = |v_s|^2 for s < count (reduction rows 0 .. count-1)
+__global__ void __launch_bounds__(kThreads) k_norms(Engine e, const double2* __restrict__ v, int64_t n,
+                                                     int64_t npad) {
+    const int s = blockIdx.y;
+    const double2* vs = v + (size_t)s * npad;
+    double local = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        local += sq(vs[i]);
+    double tot;
+    if (reduce_last_n(e, s, local, tot, gridDim.x, blockIdx.x) && threadIdx.x == 0) e.out_red[s] = tot;
+}
+
+static dim3 poly_grid(const void* fn, int64_t n, int count) {
+    return dim3(std::max(1, resident_grid(fn, n) / std::max(1, count)), count);
+}
+
+cudaError_t launch_poly_step(double2* v, const double2* Av, const ShiftCoef& a, const double2* b, int S,
+                             int64_t n, int64_t npad, cudaStream_t st) {
+    k_poly_step<<<poly_grid((const void*)k_poly_step, n, S), kThreads, 0, st>>>(v, Av, a, b, n, npad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poly_combine(double2* x, const double2* x0, const ShiftCoef& c, int S, int64_t n, int64_t npad,
+                                cudaStream_t st) {
+    k_poly_combine<<<poly_grid((const void*)k_poly_combine, n, S), kThreads, 0, st>>>(x, x0, c, n, npad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norms(const Engine& e, const double2* v, int count, int64_t n, int64_t npad, cudaStream_t st) {
+    k_norms<<<poly_grid((const void*)k_norms, n, count), kThreads, 0, st>>>(e, v, n, npad);
+    return cudaGetLastError();
 }
 
 int grid_blocks(int64_t work, int num_sms) {
@@ -312,7 +477,9 @@ static dim3 vgrid(K kernel, int64_t upv, int units_per_thread, int nsys, bool pe
 
 cudaError_t launch_init(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
                         int nsys, cudaStream_t st) {
-    if (prec == PREC_F32) k_init<float><<<vgrid(k_init<float>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys);
+    if (prec == PREC_F32 && v.pl_nc == 3) k_init_pl<3><<<multi_grid((const void*)k_init_pl<3>, v.pl_V, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys);
+    else if (prec == PREC_F32 && v.pl_nc == 2) k_init_pl<2><<<multi_grid((const void*)k_init_pl<2>, v.pl_V, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys);
+    else if (prec == PREC_F32) k_init<float><<<vgrid(k_init<float>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys);
     else k_init<double><<<vgrid(k_init<double>, upv_of(prec, v), 1, nsys), kThreads, 0, st>>>(e, v, d_descs, nsys);
     return cudaGetLastError();
 }
@@ -343,7 +510,20 @@ cudaError_t launch_axpy_norm(int prec, const Engine& e, const VecSet& v, const P
 
 cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int only_ru, cudaStream_t st, const int* act,
                         bool per_system) {
+    if (v.pl_nc == 3) {
+        k_fold_pl<3><<<multi_grid((const void*)k_fold_pl<3>, v.pl_V, nsys, per_system), kThreads, 0, st>>>(e, v, only_ru, nsys, act);
+        return cudaGetLastError();
+    }
+    if (v.pl_nc == 2) {
+        k_fold_pl<2><<<multi_grid((const void*)k_fold_pl<2>, v.pl_V, nsys, per_system), kThreads, 0, st>>>(e, v, only_ru, nsys, act);
+        return cudaGetLastError();
+    }
     k_fold<<<vgrid(k_fold, v.npad / 2, 1, nsys, per_system), kThreads, 0, st>>>(e, v, only_ru, nsys, act);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_planar(const void* src, void* dst, int nc, int V, bool to_planar, cudaStream_t st) {
+    k_convert_pl<<<resident_grid((const void*)k_convert_pl, V), kThreads, 0, st>>>(src, dst, nc, V, to_planar ? 1 : 0);
     return cudaGetLastError();
 }
 

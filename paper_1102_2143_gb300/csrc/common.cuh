@@ -76,6 +76,8 @@ struct SlotScalars {
     int flag;                           // this iteration: 0 skip, 1 x only, 2 x and p_s
     int conv_iter;                      // iteration at which tol was met (-1)
     int pad;
+    double tol2;                        // > 0: this shift's own tol^2 (relative to |b|^2)
+                                        //      in place of the system's
 };
 
 // One pass of an operator kernel: which vectors, which scalars, which
@@ -290,7 +292,8 @@ __device__ __forceinline__ void fin_R(const Engine& e, int j, double Rn) {
         const double z = q->zeta, zn = q->zeta_new;
         const double ratio = zn / z;
         q->beta_s = beta * ratio * ratio;
-        const bool conv = (zn * zn * Rn <= thr) || !(fabs(zn) > 1e-290);
+        const double tk = q->tol2 > 0.0 ? q->tol2 * s->bnorm2 : thr;
+        const bool conv = (zn * zn * Rn <= tk) || !(fabs(zn) > 1e-290);
         if (conv && q->conv_iter < 0) q->conv_iter = it + 1;
         if (conv && freeze) { q->active = 0; q->flag = 1; }
         else q->flag = 2;

@@ -21,7 +21,14 @@ enum {
 struct StagGeom {
     int L[4];
     int V;
+    // 0: the operator on the whole lattice. 1 + p: the parity-reduced
+    // operator m^2 - D_{p,1-p} D_{1-p,p} of a source on the sites of parity
+    // p = (x0 + x1 + x2 + x3) mod 2; its vectors hold those sites only, in
+    // site order (compressed index x / 2), and D passes alternate parities.
+    int eo = 0;
 };
+// sites a vector of the operator holds
+__host__ __device__ __forceinline__ int vlen(const StagGeom& g) { return g.eo ? (g.V >> 1) : g.V; }
 
 // Device-resident operator data.
 struct OpDev {
@@ -51,6 +58,14 @@ struct OpDev {
 cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, const Engine& e,
                              const PassDesc* d_descs, int npass, cudaStream_t st, const int* act = nullptr,
                              bool per_system = false);
+// FP32 staggered passes of several systems sharing the operator, the links
+// loaded once per group of systems (PASS_A and PASS_B of a solve stage;
+// every descriptor has a reduction row; FP32 vectors colour-planar). `act`
+// as above. stag_group_applies() says whether a pass takes this path.
+bool stag_group_applies(const OpDev& op, int prec, int kind, int npass);
+int stag_group_shape();
+cudaError_t launch_stag_group(const OpDev& op, int kind, const Engine& e, const PassDesc* d_descs, int npass,
+                              cudaStream_t st, const int* act);
 // h_desc (optional): host copy of the single pass's descriptor; a one-system
 // FP32 PASS_A then takes its source and output pointers from it as kernel
 // parameters (the device descriptor must hold the same pointers).
@@ -76,6 +91,11 @@ struct VecSet {
     double2* x64;   // [slots][npad]
     const double2* b64;  // [rhs][npad]
     int64_t npad;
+    // pl_nc > 0: the iteration-precision (FP32) vectors are colour-planar,
+    // entry (site x, colour a) at a * pl_V + x (staggered operators); the
+    // FP64 vectors stay site-major (x * pl_nc + a). 0: all site-major.
+    int pl_nc = 0;
+    int pl_V = 0;
 };
 cudaError_t launch_init(int prec, const Engine& e, const VecSet& v, const PassDesc* d_descs,
                         int nsys, cudaStream_t st);
@@ -88,6 +108,22 @@ cudaError_t launch_fold(const Engine& e, const VecSet& v, int nsys, int only_ru,
                         const int* act = nullptr, bool per_system = false);
 cudaError_t launch_convert(const void* src, int src_f32, void* dst, int dst_f32, int64_t n,
                            cudaStream_t st);
+// FP64 site-major <-> FP32 colour-planar copy of one vector of V sites x nc
+// colours (to_planar: src FP64, dst FP32; else the reverse).
+cudaError_t launch_convert_planar(const void* src, void* dst, int nc, int V, bool to_planar, cudaStream_t st);
+
+// right-hand sides of polynomial form (FP64, [s][npad] site-major vectors,
+// one launch for all S shifts): a Horner step v_s = Av_s + a_s b (Av null:
+// v_s = a_s b); the solution x_s = c_s x_s + x0_s (x0 null: c_s x_s); and
+// e.out_red[s] = |v_s|^2 for s < count (uses reduction rows 0 .. count-1).
+struct ShiftCoef {
+    double v[kMaxShifts + 1];
+};
+cudaError_t launch_poly_step(double2* v, const double2* Av, const ShiftCoef& a, const double2* b, int S,
+                             int64_t n, int64_t npad, cudaStream_t st);
+cudaError_t launch_poly_combine(double2* x, const double2* x0, const ShiftCoef& c, int S, int64_t n, int64_t npad,
+                                cudaStream_t st);
+cudaError_t launch_norms(const Engine& e, const double2* v, int count, int64_t n, int64_t npad, cudaStream_t st);
 
 // set-up kernels
 cudaError_t stag_pack_links(OpDev& op, const double2* links_aos, double* d_maxdev,
@@ -97,6 +133,11 @@ cudaError_t stag_unitarity(const OpDev& op, const double2* links_aos, double* d_
 cudaError_t stag_pack_links32(OpDev& op, const double2* links_aos, cudaStream_t st);
 cudaError_t stag_export_bsr(const OpDev& op, int64_t* row_ptr, int32_t* col, double2* vals,
                             cudaStream_t st);
+// max |A_ij - conj(A_ji)| and max |A_ij| over the entries of a block-CSR
+// matrix (repeated columns summed) into d_out[0], d_out[1] (FP64 bit
+// patterns; d_out zeroed by the caller).
+cudaError_t bsr_check_hermitian(const int64_t* d_row_ptr, const int32_t* d_col, const double2* d_vals,
+                                int64_t nbr, int bd, unsigned long long* d_out, cudaStream_t st);
 cudaError_t bsr_pack(OpDev& op, const int64_t* d_row_ptr, const int32_t* d_col,
                      const double2* d_vals, int* d_bad, cudaStream_t st);
 

@@ -14,6 +14,7 @@
 // FP32, SU(3) links keep two rows (third = conj(row0 x row1)) and SU(2)
 // links keep one row (second = (-conj u01, conj u00)).
 #include <algorithm>
+#include <cstdlib>
 
 #include "stencil.cuh"
 
@@ -37,8 +38,9 @@ k_stag(Engine e, const PassDesc* descs, int npass, const int* act, StagGeom g, c
     if (gated_off(e, d)) return;
     const T alpha = (KIND == PASS_B || KIND == PASS_BC) ? (T)e.sys[d.sys].alpha : T(0);
     double local = 0.0;
-    for (int x = q.bx * blockDim.x + threadIdx.x; x < g.V; x += q.gx * blockDim.x)
-        local += stag_site<T, NC, RECON, KIND, TO>(d, g, links, alpha, x);
+    const int nh = vlen(g);
+    for (int h = q.bx * blockDim.x + threadIdx.x; h < nh; h += q.gx * blockDim.x)
+        local += stag_site<T, NC, RECON, KIND, TO, true>(d, g, links, alpha, pass_site<KIND == PASS_A>(h, g));
     if (d.row >= 0) {
         double tot;
         if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize<KIND == PASS_BC>(e, d, tot);
@@ -49,7 +51,7 @@ template <class T, int NC, int RECON, int KIND, class TO>
 static void launch_one(const Engine& e, const PassDesc* descs, StagGeom g, const void* links, int npass,
                        const int* act, bool per, cudaStream_t st) {
     auto k = k_stag<T, NC, RECON, KIND, TO>;
-    k<<<multi_grid((const void*)k, g.V, npass, per), kThreads, 0, st>>>(e, descs, npass, act, g, links);
+    k<<<multi_grid((const void*)k, vlen(g), npass, per), kThreads, 0, st>>>(e, descs, npass, act, g, links);
 }
 
 template <class T, int NC, int RECON>
@@ -84,6 +86,243 @@ cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, c
     }
     if (op.recon) return launch_kind<float, 2, 1>(kind, out_f32, e, d_descs, op.g, op.links32, npass, act, per, st);
     return launch_kind<float, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links32, npass, act, per, st);
+}
+
+// ---------------------------------------------------------------------------
+// Several systems of one operator in one FP32 pass (right-hand sides of a
+// multi-shift stage, or the shifts of a refinement round): each thread takes
+// one site for up to NR systems: per hop it loads the NR neighbour spinors
+// (colour-planar vectors, so each load of a warp is one contiguous run),
+// then loads and rebuilds the link once and applies it to all of them, so a
+// pass reads the links once per group of NR systems instead of once per
+// system. The staggered phase eta_mu(x)/2 is folded into the link.
+//
+// The systems still iterating ({count, indices} in `act`, or all npass) are
+// cut into ceil(count / NR) groups of near-equal size; block b serves group
+// b % groups as its block b / groups (the groups of one site range run side
+// by side, so the second group's link loads hit L2). Per system the epilogue
+// is that of stag_site (PASS_A: out = D src, P terms; PASS_B/BC: r -= alpha
+// (d aux - D src), |r|^2), and the reductions of a group complete together:
+// its blocks publish one partial per system, then count themselves on the
+// counter of the group's first system; the last block finalizes every
+// system of the group in turn.
+// ---------------------------------------------------------------------------
+template <int NC, int RECON, int KIND, int NR, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+k_stag_group(Engine e, const PassDesc* descs, int npass, const int* act, StagGeom g, const void* links) {
+    static_assert(NR <= kThreads / 32, "one warp per system of a group reduces its partial");
+    using F2 = float2;
+    __shared__ PassDesc sd[NR];
+    __shared__ float sal[NR];
+    __shared__ int son[NR];
+    __shared__ double sred[NR][kThreads / 32];
+    __shared__ int s_last;
+    const int count = act ? __ldg(act) : npass;
+    if (count <= 0) return;
+    const int ng = (count + NR - 1) / NR;
+    const int gi = (int)(blockIdx.x % ng);
+    const int bx = (int)(blockIdx.x / ng);
+    const int gx = (int)(gridDim.x / ng);
+    if (bx >= gx) return;
+    const int lo = (int)((int64_t)gi * count / ng);
+    const int nr = (int)((int64_t)(gi + 1) * count / ng) - lo;
+    if (threadIdx.x < NR) {
+        const int r = threadIdx.x;
+        int on = 0;
+        float al = 0.f;
+        if (r < nr) {
+            const int j = act ? __ldg(act + 1 + lo + r) : lo + r;
+            const PassDesc d = descs[j];
+            sd[r] = d;
+            on = gated_off(e, d) ? 0 : 1;
+            if (on && (KIND == PASS_B || KIND == PASS_BC)) al = (float)e.sys[d.sys].alpha;
+        }
+        son[r] = on;
+        sal[r] = al;
+    }
+    __syncthreads();
+    unsigned mask = 0;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) mask |= son[r] ? (1u << r) : 0u;
+    if (mask == 0) return;
+    const int V = vlen(g);  // sites (and colour-plane stride) of the vectors
+    double local[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) local[r] = 0.0;
+    for (int h = bx * blockDim.x + threadIdx.x; h < V; h += gx * blockDim.x) {
+        const int x = pass_site<KIND == PASS_A>(h, g);
+        const SiteNbrs nb = neighbours(x, g);
+        F2 y[NR][NC];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+            for (int a = 0; a < NC; ++a) y[r][a] = {0.f, 0.f};
+#pragma unroll
+        for (int hop = 0; hop < 8; ++hop) {
+            // direction mu = hop / 2, forward (even hop) or backward
+            const int mu = hop >> 1;
+            const bool fwd = (hop & 1) == 0;
+            const int xn = fwd ? nb.fwd[mu] : nb.bwd[mu];
+            const int hn = vsite(xn, g);
+            // the neighbour spinors of every system first (colour-planar:
+            // each load of the warp is one contiguous run), then the link
+            F2 v[NR][NC];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (!((mask >> r) & 1u)) continue;
+                const F2* __restrict__ src = (const F2*)sd[r].src;
+#pragma unroll
+                for (int b = 0; b < NC; ++b) v[r][b] = src[(size_t)b * V + hn];
+            }
+            F2 u[NC][NC];
+            Links<float, NC, RECON>::load(links, mu, fwd ? x : xn, g.V, u);
+            const float eta = nb.par[mu] ? -0.5f : 0.5f;
+#pragma unroll
+            for (int a = 0; a < NC; ++a)
+#pragma unroll
+                for (int b = 0; b < NC; ++b) u[a][b] = {eta * u[a][b].x, eta * u[a][b].y};
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (!((mask >> r) & 1u)) continue;
+#pragma unroll
+                for (int a = 0; a < NC; ++a)
+#pragma unroll
+                    for (int b = 0; b < NC; ++b) {
+                        if (fwd) cfma(y[r][a], u[a][b], v[r][b]);       // + eta U_mu(x) src(x+mu)
+                        else cfms_conj(y[r][a], u[b][a], v[r][b]);      // - eta U_mu(x-mu)^dag src(x-mu)
+                    }
+            }
+        }
+    // epilogues
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (!((mask >> r) & 1u)) continue;
+            const PassDesc& d = sd[r];
+            const float dd = (float)d.d;
+            const F2* __restrict__ aux = (const F2*)d.aux + h;
+            F2* __restrict__ out = (F2*)d.out + h;
+            float loc = 0.f;
+            if (KIND == PASS_A) {
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    out[(size_t)a * V] = y[r][a];
+                    const F2 pa = aux[(size_t)a * V];
+                    loc += dd * (pa.x * pa.x + pa.y * pa.y) + y[r][a].x * y[r][a].x + y[r][a].y * y[r][a].y;
+                }
+            } else {
+                const float al = sal[r];
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const F2 pa = aux[(size_t)a * V];
+                    F2 ra = out[(size_t)a * V];
+                    ra.x -= al * (dd * pa.x - y[r][a].x);
+                    ra.y -= al * (dd * pa.y - y[r][a].y);
+                    out[(size_t)a * V] = ra;
+                    loc += ra.x * ra.x + ra.y * ra.y;
+                }
+            }
+            local[r] += (double)loc;
+        }
+    }
+    if (sd[0].row < 0) return;  // apply-only passes reduce nothing
+    // one partial per system of the group, then the group's arrival count
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const double v = warp_sum(local[r]);
+        if (lane == 0) sred[r][w] = v;
+    }
+    __syncthreads();
+    if (w < nr && ((mask >> w) & 1u)) {
+        double t = lane < (int)(blockDim.x >> 5) ? sred[w][lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) e.partial[(size_t)sd[w].row * kMaxBlocks + bx] = t;
+    }
+    __syncthreads();
+    unsigned* ctr = &e.counter[sd[0].row];
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(ctr, 1u);
+        s_last = (t == (unsigned)gx - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int r = 0; r < nr; ++r) {
+        if (!((mask >> r) & 1u)) continue;
+        const PassDesc d = sd[r];
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < gx; i += blockDim.x) acc += __ldcg(&e.partial[(size_t)d.row * kMaxBlocks + i]);
+        const double tot = block_sum(acc, &sred[0][0]);
+        __shared__ double s_tot;
+        if (threadIdx.x == 0) s_tot = tot;
+        __syncthreads();
+        finalize<KIND == PASS_BC>(e, d, s_tot);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ctr = 0u;
+}
+
+template <int NC, int RECON, int NR, int MINB>
+static cudaError_t launch_group_kind(int kind, const Engine& e, const PassDesc* descs, StagGeom g,
+                                     const void* links, int npass, const int* act, cudaStream_t st) {
+    const int groups = (npass + NR - 1) / NR;
+    switch (kind) {
+        case PASS_A: {
+            auto k = k_stag_group<NC, RECON, PASS_A, NR, MINB>;
+            k<<<multi_grid((const void*)k, vlen(g), groups), kThreads, 0, st>>>(e, descs, npass, act, g, links);
+            break;
+        }
+        case PASS_B:
+            if (e.cond_flag) {
+                auto k = k_stag_group<NC, RECON, PASS_BC, NR, MINB>;
+                k<<<multi_grid((const void*)k, vlen(g), groups), kThreads, 0, st>>>(e, descs, npass, act, g, links);
+            } else {
+                auto k = k_stag_group<NC, RECON, PASS_B, NR, MINB>;
+                k<<<multi_grid((const void*)k, vlen(g), groups), kThreads, 0, st>>>(e, descs, npass, act, g, links);
+            }
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Launch shape of the grouped passes, 10 * systems per thread + blocks per
+// SM: 21, 22, 42, 43 or 82; 0 runs every system through k_stag instead.
+int stag_group_shape() {
+    static int shape = [] {
+        const char* v = getenv("MSC_STAG_GROUP");
+        const int k = v ? atoi(v) : 43;
+        return (k == 0 || k == 21 || k == 22 || k == 42 || k == 43 || k == 82) ? k : 43;
+    }();
+    return shape;
+}
+
+bool stag_group_applies(const OpDev& op, int prec, int kind, int npass) {
+    return op.kind == OP_STAGGERED && prec == PREC_F32 && op.recon && npass >= 2 &&
+           (kind == PASS_A || kind == PASS_B) && stag_group_shape() != 0;
+}
+
+// Group shapes: NR systems per thread, MINB blocks per SM.
+template <int NC>
+static cudaError_t launch_group_nc(int shape, int kind, const Engine& e, const PassDesc* d, const OpDev& op,
+                                   int npass, const int* act, cudaStream_t st) {
+    switch (shape) {
+        case 21: return launch_group_kind<NC, 1, 2, 3>(kind, e, d, op.g, op.links32, npass, act, st);
+        case 22: return launch_group_kind<NC, 1, 2, 2>(kind, e, d, op.g, op.links32, npass, act, st);
+        case 42: return launch_group_kind<NC, 1, 4, 2>(kind, e, d, op.g, op.links32, npass, act, st);
+        case 43: return launch_group_kind<NC, 1, 4, 3>(kind, e, d, op.g, op.links32, npass, act, st);
+        default: return launch_group_kind<NC, 1, 8, 2>(kind, e, d, op.g, op.links32, npass, act, st);
+    }
+}
+
+cudaError_t launch_stag_group(const OpDev& op, int kind, const Engine& e, const PassDesc* d_descs, int npass,
+                              cudaStream_t st, const int* act) {
+    int shape = stag_group_shape();
+    if (npass <= 2 && shape > 22) shape = 21;
+    if (npass <= 4 && shape > 43) shape = 43;
+    if (op.nc == 3) return launch_group_nc<3>(shape, kind, e, d_descs, op, npass, act, st);
+    return launch_group_nc<2>(shape, kind, e, d_descs, op, npass, act, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -35,6 +35,33 @@ __device__ __forceinline__ SiteNbrs neighbours(int x, const StagGeom& g) {
     return nb;
 }
 
+// Parity-reduced operator (g.eo = 1 + p): site x sits at compressed index
+// x / 2 of a parity vector (each pair of sites (2k, 2k+1) along x0 holds one
+// site of each parity), and the h-th site of parity par is eo_site(h, par).
+__device__ __forceinline__ int vsite(int x, const StagGeom& g) { return g.eo ? (x >> 1) : x; }
+
+__device__ __forceinline__ int eo_site(int h, int par, const StagGeom& g) {
+    const int hl = g.L[0] >> 1;
+    const int row = h / hl;
+    const int k = h - row * hl;
+    int r = row;
+    const int c1 = r % g.L[1];
+    r /= g.L[1];
+    const int c2 = r % g.L[2];
+    const int c3 = r / g.L[2];
+    return 2 * k + ((par + c1 + c2 + c3) & 1) + g.L[0] * row;
+}
+
+// The site a thread of a pass handles at loop index h: on the
+// parity-reduced operator, t = D p (PASS_A, OTHER) lives on the other parity
+// and every other pass's output on the source's.
+template <bool OTHER>
+__device__ __forceinline__ int pass_site(int h, const StagGeom& g) {
+    if (!g.eo) return h;
+    const int src_par = g.eo - 1;
+    return eo_site(h, OTHER ? 1 - src_par : src_par, g);
+}
+
 // ---------------------------------------------------------------------------
 // link loads
 // ---------------------------------------------------------------------------
@@ -80,8 +107,18 @@ template <> struct Links<float, 2, 1> {
     }
 };
 
+// Index of the complex entry (site x, colour a) of a vector of element type
+// T. Vectors are site-major (x * NC + a), except FP32 vectors of the
+// single-operator stencil path (PL), which are colour-planar (a * V + x): the
+// loads of one colour of a warp's 32 consecutive sites are then one
+// contiguous 256-byte run instead of three 8-byte loads at a 24-byte stride.
+template <class T, bool PL, int NC>
+__device__ __forceinline__ size_t vix(int x, int a, int V) {
+    return (PL && sizeof(T) == 4) ? (size_t)a * V + x : (size_t)x * NC + a;
+}
+
 // y = D src at site x
-template <class T, int NC, int RECON>
+template <class T, int NC, int RECON, bool PL = false>
 __device__ __forceinline__ void dslash_site(const void* links, const T2<T>* __restrict__ src, int x,
                                             const StagGeom& g, T2<T> (&y)[NC]) {
     const SiteNbrs nb = neighbours(x, g);
@@ -92,11 +129,11 @@ __device__ __forceinline__ void dslash_site(const void* links, const T2<T>* __re
         T2<T> u[NC][NC], v[NC];
         Links<T, NC, RECON>::load(links, mu, x, g.V, u);
 #pragma unroll
-        for (int b = 0; b < NC; ++b) v[b] = src[(size_t)nb.fwd[mu] * NC + b];
+        for (int b = 0; b < NC; ++b) v[b] = src[vix<T, PL, NC>(vsite(nb.fwd[mu], g), b, vlen(g))];
         T2<T> w[NC][NC], z[NC];
         Links<T, NC, RECON>::load(links, mu, nb.bwd[mu], g.V, w);
 #pragma unroll
-        for (int b = 0; b < NC; ++b) z[b] = src[(size_t)nb.bwd[mu] * NC + b];
+        for (int b = 0; b < NC; ++b) z[b] = src[vix<T, PL, NC>(vsite(nb.bwd[mu], g), b, vlen(g))];
         const T eta = nb.par[mu] ? T(-0.5) : T(0.5);
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
@@ -118,22 +155,25 @@ __device__ __forceinline__ void dslash_site(const void* links, const T2<T>* __re
 //   PASS_B: r -= alpha (d aux - y);        |r|^2
 //   PASS_C: out = b - (d aux - y) (FP64);  |out|^2
 //   PASS_D: out = d aux - y
-template <class T, int NC, int RECON, int KIND, class TO>
+// PL: FP32 vectors (of type T or TO) are colour-planar (see vix).
+template <class T, int NC, int RECON, int KIND, class TO, bool PL = false>
 __device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g, const void* links,
                                             T alpha, int x) {
     const T2<T>* __restrict__ src = (const T2<T>*)d.src;
     const T2<T>* __restrict__ aux = (const T2<T>*)d.aux;
     const T dd = (T)d.d;
+    const int V = vlen(g);
     T2<T> y[NC];
-    dslash_site<T, NC, RECON>(links, src, x, g, y);
+    dslash_site<T, NC, RECON, PL>(links, src, x, g, y);
+    x = vsite(x, g);  // the site's index in the vectors
     if (KIND == PASS_A) {
         T2<T>* out = (T2<T>*)d.out;
         T loc = T(0);
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
-            out[(size_t)x * NC + a] = y[a];
+            out[vix<T, PL, NC>(x, a, V)] = y[a];
             if (d.row >= 0) {
-                const T2<T> pa = aux[(size_t)x * NC + a];
+                const T2<T> pa = aux[vix<T, PL, NC>(x, a, V)];
                 loc += dd * (pa.x * pa.x + pa.y * pa.y) + y[a].x * y[a].x + y[a].y * y[a].y;
             }
         }
@@ -143,12 +183,12 @@ __device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g
         T loc = T(0);
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
-            const T2<T> pa = aux[(size_t)x * NC + a];
+            const T2<T> pa = aux[vix<T, PL, NC>(x, a, V)];
             const T2<T> ap = {dd * pa.x - y[a].x, dd * pa.y - y[a].y};
-            T2<T> ra = r[(size_t)x * NC + a];
+            T2<T> ra = r[vix<T, PL, NC>(x, a, V)];
             ra.x -= alpha * ap.x;
             ra.y -= alpha * ap.y;
-            r[(size_t)x * NC + a] = ra;
+            r[vix<T, PL, NC>(x, a, V)] = ra;
             loc += ra.x * ra.x + ra.y * ra.y;
         }
         return (double)loc;
@@ -157,13 +197,14 @@ __device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g
         double loc = 0.0;
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
-            const T2<T> xa = aux[(size_t)x * NC + a];
+            const T2<T> xa = aux[vix<T, PL, NC>(x, a, V)];
             const double2 ba = d.b[(size_t)x * NC + a];
             const double vx = ba.x - ((double)dd * xa.x - y[a].x);
             const double vy = ba.y - ((double)dd * xa.y - y[a].y);
             if (out) {
-                out[2 * ((size_t)x * NC + a)] = (TO)vx;
-                out[2 * ((size_t)x * NC + a) + 1] = (TO)vy;
+                const size_t o = vix<TO, PL, NC>(x, a, V);
+                out[2 * o] = (TO)vx;
+                out[2 * o + 1] = (TO)vy;
             }
             loc += vx * vx + vy * vy;
         }
@@ -172,8 +213,8 @@ __device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g
         T2<T>* out = (T2<T>*)d.out;
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
-            const T2<T> xa = aux[(size_t)x * NC + a];
-            out[(size_t)x * NC + a] = {dd * xa.x - y[a].x, dd * xa.y - y[a].y};
+            const T2<T> xa = aux[vix<T, PL, NC>(x, a, V)];
+            out[vix<T, PL, NC>(x, a, V)] = {dd * xa.x - y[a].x, dd * xa.y - y[a].y};
         }
         return 0.0;
     }

@@ -45,3 +45,31 @@ def test_solve_bytes_hand_worked_case():
 def test_spmv_bytes_of_the_benchmark_operator():
     # 24^4 block-CSR: 10,948,608 blocks of 3 x 3, 995,328 unknowns, FP32
     assert bench.spmv_bytes(10948608, 3, 995328, 4) == 848019456
+
+
+class _StagInfo:
+    """Two right-hand sides x two shifts on the stencil path (see below)."""
+    iters = 3
+    shift_iters = np.array([[3, 1], [2, 1]])
+    reliable_updates = 1
+    refine_reliable_updates = 0
+    refine_rounds = 1
+    shift_refine_iters = np.array([[0, 2], [0, 0]])
+
+
+def test_stencil_solve_bytes_hand_worked_case():
+    """V = 16 sites of SU(3), two-row FP32 links, mixed: u = 24 B per site
+    vector, l = 4 * 6 * 8 = 192 B of FP32 links and l64 = 4 * 9 * 16 = 576 B
+    of FP64 links per site; one FP64 residual = 2 * 576 + 2 * 48 + 3 * 48 +
+    24 = 1416 B per site.
+      RHS 0: k = 1 update 5 + 3 = 8 passes -> 16 * (2 + 4 + 8) * 24 = 5376;
+             k = 2, 3: 16 * 11 * 24 = 4224 each               = 13824
+      RHS 1: 5376 + 4224                                        =  9600
+      links of both passes, 3 iterations: 3 * 2 * 16 * 192     = 18432
+      folds (1 reliable update + the final one per RHS) x 2 shifts x 40 * 3 * 16
+                                                                = 11520
+      the reliable update's FP64 residual 16 * 1416             = 22656
+      checks (4 + 1 refined) * 16 * 1416                        = 113280
+      refinement k = 1, 2: 2 * 16 * 192 + 16 * 11 * 24 each     = 20736
+      total 210048 B."""
+    assert bench.stencil_solve_bytes(_StagInfo(), 2, 16, 3, 1, mixed=True) == 210048

@@ -254,6 +254,35 @@ def test_cgm_freeze_reports_per_shift_iterations():
         assert np.linalg.norm(res.x[i] - res2.x[i]) <= 1e-9 * np.linalg.norm(res2.x[i])
 
 
+def test_true_residual_exact_values():
+    """rho_s = |b - (A + sigma_s) x_s| / |b| on solutions with a planted
+    residual: x_s = (A + sigma_s)^{-1} (b - e_s) by LAPACK gives rho_s =
+    |e_s| / |b| exactly (to rounding). The planted norms differ by orders of
+    magnitude per shift, so a wrong shift index, a wrong normalisation (|b|^2,
+    no square root) or a dropped sigma fails; x = 0 gives rho = 1."""
+    dims, nc, m = (2, 2, 4, 2), 2, 0.3
+    U = inputs.su_n_links(dims, nc, 0.8, 14)
+    A = _dense_A(U, dims, nc, m)
+    n = A.shape[0]
+    b = _vec(n, 15)
+    sigma = np.array([0.0, 0.05, 2.0])
+    scale = np.array([1e-2, 1e-4, 1e-6])
+    x = np.empty((len(sigma), n), dtype=np.complex128)
+    want = np.empty(len(sigma))
+    for i, s in enumerate(sigma):
+        e = _vec(n, 16 + i)
+        e *= scale[i] * np.linalg.norm(b) / np.linalg.norm(e)
+        x[i] = np.linalg.solve(A + s * np.eye(n), b - e)
+        want[i] = np.linalg.norm(e) / np.linalg.norm(b)
+    rho = oracle.true_residual_staggered(U, dims, nc, m, b, sigma, x)
+    assert np.allclose(rho, want, rtol=1e-6, atol=0), (rho, want)
+    # the pairing of x_s with sigma_s matters
+    rho_swapped = oracle.true_residual_staggered(U, dims, nc, m, b, sigma, x[::-1].copy())
+    assert not np.allclose(rho_swapped, want[::-1], rtol=1e-2, atol=0)
+    rho0 = oracle.true_residual_staggered(U, dims, nc, m, b, sigma, np.zeros_like(x))
+    assert np.allclose(rho0, 1.0, rtol=1e-15, atol=0)
+
+
 def test_quadratic_form_bounds():
     """|phi|^2/(m^2+16+sigma) <= phi^dagger (A+sigma)^-1 phi <= |phi|^2/(m^2+sigma)
     since 0 <= -D^2 <= 16 for unitary links (|D| <= 4)."""
@@ -510,3 +539,99 @@ def test_bicgstabm_breakdown_is_reported():
     b = np.arange(1, 17, dtype=np.float64).astype(np.complex128)
     res = oracle.bicgstabm_bsr(rp, ci, va, b, [0.0], 1e-10)
     assert res.status == 7      # breakdown
+
+
+# ----------------------------------------------------------------------------
+# Different right-hand side per shift, b_s = q_s(A) b (Sec. 5, eq. linprobgen)
+# ----------------------------------------------------------------------------
+
+def _poly_coefs(S, deg, seed):
+    g = inputs.rng(seed)
+    return g.uniform(-1.0, 1.0, size=(S, deg + 1))
+
+
+def test_poly_rhs_matches_dense_solves():
+    """x_s = (A + sigma_s)^{-1} q_s(A) b against LAPACK, with q_s(A) formed
+    from dense matrix powers (not Horner's rule)."""
+    dims, nc, m = (2, 4, 2, 4), 2, 0.2
+    U = inputs.su_n_links(dims, nc, 0.6, 17)
+    A = _dense_A(U, dims, nc, m)
+    n = A.shape[0]
+    b = _vec(n, 18)
+    sig = np.array([0.0, 0.01, 0.5, 3.0])
+    coef = _poly_coefs(len(sig), 3, 19)
+    x, bs = oracle.solve_poly_rhs_staggered(U, dims, nc, m, b, sig, coef, 1e-13)
+    for s in range(len(sig)):
+        Q = sum(coef[s, k] * np.linalg.matrix_power(A, k) for k in range(coef.shape[1]))
+        want_b = Q @ b
+        assert np.linalg.norm(bs[s] - want_b) <= 1e-12 * np.linalg.norm(want_b)
+        want = np.linalg.solve(A + sig[s] * np.eye(n), want_b)
+        assert np.linalg.norm(x[s] - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_poly_rhs_constant_polynomials_reduce_to_cgm():
+    """q_s = c_s (degree 0) gives c_s times the one-source CG-M solution."""
+    p = inputs.lattice_4x4_su3_8shifts()
+    c = np.linspace(0.5, 2.0, len(p.sigma))[:, None]
+    x, _ = oracle.solve_poly_rhs_staggered(p.links, p.dims, p.nc, p.mass, p.b[0], p.sigma, c, 1e-13)
+    ref = oracle.cgm_staggered(p.links, p.dims, p.nc, p.mass, p.b[0], p.sigma, 1e-13)
+    for s in range(len(p.sigma)):
+        want = c[s, 0] * ref.x[s]
+        assert np.linalg.norm(x[s] - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_poly_rhs_division_gives_collinear_initial_residuals():
+    """The construction the GPU path uses: dividing q_s(t) by (t + sigma_s)
+    gives q_s(t) = q_s(-sigma_s) + (t + sigma_s) s_s(t), so the initial guess
+    x_s0 = s_s(A) b leaves the residual b_s - (A + sigma_s) x_s0 =
+    q_s(-sigma_s) b, collinear with b for every shift (one CG-M sequence on b
+    then serves all shifts). Checked with numpy's polynomial division and the
+    oracle's operator."""
+    p = inputs.lattice_4x4_su3_8shifts()
+    coef = _poly_coefs(len(p.sigma), 4, 20)
+    b = p.b[0]
+    for s, sg in enumerate(p.sigma):
+        quo, rem = np.polynomial.polynomial.polydiv(coef[s], [sg, 1.0])
+        c = np.polynomial.polynomial.polyval(-sg, coef[s])
+        assert abs(rem[0] - c) <= 1e-13 * max(1.0, abs(c))
+        x0 = oracle.poly_apply_staggered(p.links, p.dims, p.nc, p.mass, quo, b)
+        bs = oracle.poly_apply_staggered(p.links, p.dims, p.nc, p.mass, coef[s], b)
+        r0 = bs - oracle.staggered_apply(p.links, p.dims, p.nc, p.mass, x0, sigma=sg)
+        assert np.linalg.norm(r0 - c * b) <= 1e-12 * np.linalg.norm(bs)
+
+
+# ----------------------------------------------------------------------------
+# Parity: A = m^2 - D^2 couples no even site to an odd one
+# ----------------------------------------------------------------------------
+
+def _site_parity(dims):
+    V = inputs.volume(dims)
+    x = np.arange(V)
+    c0 = x % dims[0]
+    c1 = (x // dims[0]) % dims[1]
+    c2 = (x // (dims[0] * dims[1])) % dims[2]
+    c3 = x // (dims[0] * dims[1] * dims[2])
+    return (c0 + c1 + c2 + c3) & 1
+
+
+@pytest.mark.parametrize("par", [0, 1])
+def test_parity_sources_stay_on_their_parity(par):
+    """D maps one parity to the other, so A maps a parity-p vector to a
+    parity-p vector and the CG-M solution of a parity-p source is zero on the
+    other parity: the reduced solve of that parity alone is exact. The sites
+    of one parity, in site order, are exactly the sites x with index x // 2
+    (one per pair (2k, 2k+1) along x0)."""
+    dims, nc, m = (4, 6, 4, 4), 3, 0.15
+    U = inputs.su_n_links(dims, nc, 0.7, 21)
+    P = _site_parity(dims)
+    sites = np.nonzero(P == par)[0]
+    assert np.array_equal(sites // 2, np.arange(len(sites)))
+    mask = np.repeat(P == par, nc)
+    v = _vec(inputs.volume(dims) * nc, 22) * mask
+    Dv = oracle.dslash(U, dims, nc, v)
+    assert np.all(Dv[mask] == 0)
+    Av = oracle.staggered_apply(U, dims, nc, m, v, sigma=0.3)
+    assert np.all(Av[~mask] == 0)
+    res = oracle.cgm_staggered(U, dims, nc, m, v, [0.0, 0.1, 1.0], 1e-12)
+    assert res.status == 0
+    assert np.all(res.x[:, ~mask] == 0)

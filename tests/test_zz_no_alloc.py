@@ -2,15 +2,17 @@
 let a library allocate device memory (code under another framework's memory
 pool or allocator, latency-bound loops where cudaMalloc may block or fail).
 
-Its result must equal msc_op_apply's (which stages vectors in a workspace it
-allocates) to the FP64 operator tolerance of the other GPU tests, 1e-13
-relative, on two calls in a row: the second call reuses the fixed scratch
-array the first one left behind. Collected last so that a failure here does
-not hide the rest of the suite; it also passes on its own in a fresh process.
+Its result must equal the oracle's FP64 (A + sigma) x and msc_op_apply's
+(which stages vectors in a workspace it allocates), both to the FP64 operator
+tolerance of the other GPU tests, 1e-13 relative, on two calls in a row: the
+second call reuses the fixed scratch array the first one left behind.
+Collected last so that a failure here does not hide the rest of the suite; it
+also passes on its own in a fresh process.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1102_2143_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +50,10 @@ def test_noalloc_apply_equals_allocating_apply(ctx, nc, dims, sigma):
         msc.msc_op_apply_noalloc(op, sigma, x, out, stream)
         torch.cuda.synchronize()
         assert rel(out, ref) <= TOL, (call, rel(out, ref))
+        want = oracle.staggered_apply(U, dims, nc, 0.1, x.cpu().numpy(), sigma)
+        got = out.cpu().numpy()
+        err = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert err <= TOL, (call, err)
     msc.msc_op_destroy(op)
 
 
@@ -77,6 +83,11 @@ def test_noalloc_apply_allocates_nothing_and_rejects_oversize(ctx):
     with pytest.raises(msc.MscError) as e:
         msc.msc_op_apply_noalloc(op, 0.1, x.cpu().numpy(), out, stream)
     assert e.value.code == msc.MSC_ERR_ARG
+    # the binding refuses a tensor of the wrong type or length before the call
+    with pytest.raises(ValueError):
+        msc.msc_op_apply_noalloc(op, 0.1, x.to(torch.complex64), out, stream)
+    with pytest.raises(ValueError):
+        msc.msc_op_apply_noalloc(op, 0.1, x[:-1], out[:-1], stream)
     msc.msc_op_destroy(op)
     # more than 2^20 complex unknowns does not fit the fixed array
     big = (32, 32, 32, 12)
