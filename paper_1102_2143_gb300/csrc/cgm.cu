@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(kThreads) k_axpy_norm(Engine e, VecSet v, cons
 }
 
 // x_s(FP64) += x_s(FP32 accumulator); accumulator = 0, for every shift of
-// the system (mixed precision; runs whatever the system's status).
+// the system with something to fold (mixed precision; runs whatever the
+// system's status).
 __global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v, int only_ru, int nsys, const int* act) {
     const SysBlock sb = sys_block(nsys, act);
     if (!sb.ok) return;
@@ -278,11 +279,12 @@ __global__ void __launch_bounds__(kThreads) k_fold(Engine e, VecSet v, int only_
     const int st = load_status(s);
     if (st == ST_ERR_NOT_HPD || st == ST_ERR_NONFINITE) return;
     if (only_ru && (st != ST_RUNNING || __ldcg(&s->ru) == 0)) return;
-    const int S = s->S, slot0 = s->slot0;
+    const int S = s->S, slot0 = s->slot0, lf = s->last_fold;
     const int64_t upv = v.npad / 2;
     float4* xa = (float4*)v.xit;
     for (int64_t i = sb.bx * (int64_t)blockDim.x + threadIdx.x; i < upv; i += (int64_t)sb.gx * blockDim.x) {
         for (int k = 0; k < S; ++k) {
+            if (fold_skips(&e.slot[slot0 + k], lf)) continue;
             const size_t g = (size_t)(slot0 + k);
             const float4 dx = xa[g * upv + i];
             double2* x = v.x64 + g * v.npad + 2 * i;
@@ -306,11 +308,12 @@ __global__ void __launch_bounds__(kThreads) k_fold_pl(Engine e, VecSet v, int on
     const int st = load_status(s);
     if (st == ST_ERR_NOT_HPD || st == ST_ERR_NONFINITE) return;
     if (only_ru && (st != ST_RUNNING || __ldcg(&s->ru) == 0)) return;
-    const int S = s->S, slot0 = s->slot0;
+    const int S = s->S, slot0 = s->slot0, lf = s->last_fold;
     const int V = v.pl_V;
     float2* xa = (float2*)v.xit;
     for (int64_t x = sb.bx * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)sb.gx * blockDim.x) {
         for (int k = 0; k < S; ++k) {
+            if (fold_skips(&e.slot[slot0 + k], lf)) continue;
             const size_t g = (size_t)(slot0 + k) * v.npad;
             double2* xs = v.x64 + g + x * NC;
 #pragma unroll

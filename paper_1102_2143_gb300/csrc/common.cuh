@@ -65,7 +65,7 @@ struct SysScalars {
     int since_ru;     // iterations since the last reliable update
     int ru;           // 1: the reliable-update kernels of this iteration run
     int nru;          // reliable updates done
-    int pad0;
+    int last_fold;    // iteration count at the last reliable update's fold
 };
 
 struct SlotScalars {
@@ -354,8 +354,18 @@ __device__ __forceinline__ void fin_setR(const Engine& e, int j, double Rv, bool
         s->Rmax = Rv;
         s->since_ru = 0;
         s->ru = 0;
-        if (!init) s->nru += 1;
+        if (!init) {
+            s->nru += 1;
+            s->last_fold = s->it;  // the update's fold ran before this residual
+        }
     }
+}
+
+// A fold of the system's FP32 x accumulators skips slot k when nothing has
+// been added to it since the last fold: it stopped iterating (frozen at
+// conv_iter, its last x update) no later than that fold.
+__device__ __forceinline__ bool fold_skips(const SlotScalars* q, int last_fold) {
+    return !q->active && q->conv_iter >= 0 && q->conv_iter <= last_fold;
 }
 
 __device__ __forceinline__ void fin_init(const Engine& e, int j, double b2) {
