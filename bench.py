@@ -226,7 +226,8 @@ def stencil_solve_bytes(info, S, V, nc, recon, mixed=True):
         fold = 40 * nc * V
         total += (ru_main + R) * S * fold
         total += ru_main * V * res64
-        total += int(info.refine_reliable_updates) * V * (res64 + fold)
+        # refinement-stage updates: one FP64 residual and the fold of one shift
+        total += int(info.refine_reliable_updates) * (V * res64 + fold)
     ref = np.asarray(info.shift_refine_iters).reshape(-1)
     refined = int(np.count_nonzero(ref))
     total += (R * S + refined * int(info.refine_rounds)) * V * res64
@@ -673,9 +674,11 @@ def other_workloads(ctx, msc, inputs, torch, stream):
                     "4..20 shifts 1e-4..1, 4 RHS each, mixed, tol 1e-10",
         "batched_ms": ms_b, "one_by_one_ms": ms_s, "speedup": ms_s / ms_b,
         "algorithmic_bytes": bbytes, "batched_gbs": bbytes / (ms_b * 1e-3) / 1e9,
-        "batched_frac": bbytes / (ms_b * 1e-3) / 1e9 / peak,
+        "batched_over_hbm_copy": bbytes / (ms_b * 1e-3) / 1e9 / peak,
         "one_by_one_gbs": bbytes / (ms_s * 1e-3) / 1e9,
-        "bytes": "sum over the 64 problems of the stencil solve's algorithmic bytes (bench.stencil_solve_bytes)",
+        "bytes": "sum over the 64 problems of the stencil solve's algorithmic bytes (bench.stencil_solve_bytes); "
+                 "the systems are small (at most 12^4 sites, vectors of at most 0.5 MB), so their working "
+                 "sets stay in the 129 MB L2 and the rate can exceed the HBM copy bandwidth",
         "tuned_shape": {"site_threads": tun.site_threads, "vec_threads": tun.vec_threads,
                         "vec_units": tun.vec_units}}
     for o in ops:

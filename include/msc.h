@@ -49,7 +49,9 @@ extern "C" {
 #define MSC_ERR_NOT_HPD       4  /* p^dagger A p <= 0 met: A is not positive definite */
 #define MSC_ERR_NONFINITE     5  /* NaN or Inf met in the source or the iteration */
 #define MSC_ERR_NOT_CONVERGED 6  /* iteration cap reached; x is written, see info */
-#define MSC_ERR_TIMEOUT       7  /* reserved: a bounded device wait gave up */
+#define MSC_ERR_TIMEOUT       7  /* a kernel's bounded wait on its own asynchronous
+                                    copies ran out (the solve's results are void;
+                                    the context stays usable) */
 #define MSC_ERR_UNSUPPORTED   8  /* valid request the library does not handle */
 #define MSC_ERR_BREAKDOWN     9  /* msc_solve_nonherm: a BiCGStab denominator vanished */
 

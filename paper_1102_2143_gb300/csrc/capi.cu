@@ -78,6 +78,11 @@ struct msc_ctx {
     Buf bcg;          // BiCGStab-M scalars: one BcgSys, then S BcgSlot
     Buf condf;        // one flag per iteration of a chunk graph (conditional update bodies)
     Buf pb, px0, ptmp;// polynomial right-hand sides: b_s, x_s0, two scratch vectors per shift
+    Buf errf;         // device error word (bit 0: a bounded wait in a kernel ran out)
+    unsigned* h_err = nullptr;  // pinned copy of it
+    uint64_t wait_ns = 2000000000ull;  // limit of a kernel's wait on its own copies
+    int use_tile = 0;  // one-system FP32 stencil passes stage their links (when the lattice tiles)
+    int test_no_copy = 0;  // tests only: the staged passes issue no copies, so their waits run out
     int use_cond = 1; // build reliable updates as conditional graph nodes
     int* h_flags = nullptr;  // pinned copy of the conditional flags of a chunk
     int* h_act = nullptr;
@@ -167,9 +172,11 @@ static int ensure_ws(msc_ctx* c, int64_t npad, int64_t rows, int64_t slots, int6
     CK(grow(c, c->b64, (size_t)rhs * npad * 16, moved));
     CK(grow(c, c->x64, (size_t)slots * npad * 16, moved));
     CK(grow(c, c->t64, (size_t)std::max(rows, slots) * npad * 16, moved));
-    CK(grow(c, c->r, (size_t)R * npad * elem, moved));
-    CK(grow(c, c->p, (size_t)R * npad * elem, moved));
-    CK(grow(c, c->t, (size_t)R * npad * elem, moved));
+    // per-system vectors: this call's rows (rows_cap only lays out the
+    // descriptor sections; a large batch before must not scale them)
+    CK(grow(c, c->r, (size_t)rows * npad * elem, moved));
+    CK(grow(c, c->p, (size_t)rows * npad * elem, moved));
+    CK(grow(c, c->t, (size_t)rows * npad * elem, moved));
     CK(grow(c, c->ps, (size_t)slots * npad * elem, moved));
     CK(grow(c, c->xit, (size_t)slots * npad * 8, moved));
     if (moved) c->gen++;
@@ -204,6 +211,7 @@ static Engine engine_of(msc_ctx* c) {
     e.partial = (double*)c->partial.p;
     e.counter = (unsigned*)c->counter.p;
     e.out_red = (double*)c->out_red.p;
+    e.err = (unsigned*)c->errf.p;
     return e;
 }
 
@@ -255,6 +263,9 @@ static cudaError_t op_pass(msc_ctx* c, const OpDev& A, int prec, int kind, int o
     Engine e = eng ? *eng : engine_of(c);
     c->launches++;
     if (A.kind == OP_STAGGERED) {
+        if (!per_system && npass == 1 && prec == PREC_F32 && (kind == PASS_A || kind == PASS_B) && A.recon &&
+            c->use_tile && stag_tile_fits(A.g, A.nc))
+            return launch_stag_tile(A, kind, e, dsec(c, sec), c->wait_ns, c->test_no_copy, c->work);
         if (!per_system && stag_group_applies(A, prec, kind, npass))
             return launch_stag_group(A, kind, e, dsec(c, sec), npass, c->work, act);
         return launch_stag_pass(A, prec, kind, out_f32, e, dsec(c, sec), npass, c->work, act, per_system);
@@ -540,7 +551,14 @@ static int run_stage(msc_ctx* c, const msc_op* op, int prec, int nsys, int chunk
         if (track)
             CK(cudaMemcpyAsync(c->h_slot, c->slot.p, sizeof(SlotScalars) * nslot_all, cudaMemcpyDeviceToHost,
                                c->work));
+        CK(cudaMemcpyAsync(c->h_err, c->errf.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->work));
         CK(cudaStreamSynchronize(c->work));
+        if (*c->h_err) {
+            // a kernel's bounded wait ran out: the chunk's results are void
+            CK(cudaMemsetAsync(c->errf.p, 0, sizeof(unsigned), c->work));
+            CK(cudaStreamSynchronize(c->work));
+            return MSC_ERR_TIMEOUT;
+        }
         for (int i = 0; i < ncf; ++i) c->launches += c->h_flags[i] ? ge->cond_kernels : 0;
         if (track && all_running) {
             float a = 0, b = 0, d = 0;
@@ -637,9 +655,27 @@ int msc_create(msc_ctx** out, int device, void* stream) {
     // exit when no update is due, instead of conditional graph nodes (for
     // profilers that replay kernels one by one)
     if (const char* ev = getenv("MSC_GRAPH_COND")) c->use_cond = atoi(ev) != 0;
+    // MSC_STAG_TILE=1: one-system FP32 stencil passes stage their links in
+    // shared memory by bulk asynchronous copies (lattices that tile; off by
+    // default, the direct passes are faster). MSC_WAIT_NS: the limit of a
+    // kernel's wait on its own asynchronous copies. MSC_TEST_NO_COPY=1 (tests
+    // of the timeout path only): the staged passes issue no copies.
+    if (const char* ev = getenv("MSC_STAG_TILE")) c->use_tile = atoi(ev) != 0;
+    if (const char* ev = getenv("MSC_WAIT_NS")) {
+        const long long w = atoll(ev);
+        if (w > 0) c->wait_ns = (uint64_t)w;
+    }
+    if (const char* ev = getenv("MSC_TEST_NO_COPY")) c->test_no_copy = atoi(ev) != 0;
     cudaError_t e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sync, cudaEventDisableTiming);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->prof[i]);
+    if (e == cudaSuccess) e = cudaMalloc(&c->errf.p, 16);
+    if (e == cudaSuccess) {
+        c->errf.bytes = 16;
+        e = cudaMemsetAsync(c->errf.p, 0, 16, c->work);
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
     if (e != cudaSuccess) {
         msc_destroy(c);
         return cuda_status(e);
@@ -663,7 +699,7 @@ int msc_destroy(msc_ctx* c) {
     Buf* bufs[] = {&c->sys, &c->slot, &c->partial, &c->counter, &c->out_red, &c->descs,
                    &c->b64, &c->x64, &c->t64, &c->r, &c->p, &c->t, &c->ps, &c->xit,
                    &c->coef, &c->force, &c->btab, &c->actb, &c->condf, &c->bcg,
-                   &c->pb, &c->px0, &c->ptmp};
+                   &c->pb, &c->px0, &c->ptmp, &c->errf};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_sys) cudaFreeHost(c->h_sys);
@@ -672,6 +708,7 @@ int msc_destroy(msc_ctx* c) {
     if (c->h_desc) cudaFreeHost(c->h_desc);
     if (c->h_act) cudaFreeHost(c->h_act);
     if (c->h_flags) cudaFreeHost(c->h_flags);
+    if (c->h_err) cudaFreeHost(c->h_err);
     if (c->ev_sync) cudaEventDestroy(c->ev_sync);
     for (int i = 0; i < 4; ++i)
         if (c->prof[i]) cudaEventDestroy(c->prof[i]);

@@ -105,6 +105,9 @@ struct Engine {
     // and the flag that lets exactly one system set it
     unsigned long long cond;
     int* cond_flag;
+    // error word (bit 0: a bounded wait of a kernel ran out), read by the host
+    // after each launch chunk; may be null
+    unsigned* err;
 };
 
 // ---------------------------------------------------------------------------

@@ -66,6 +66,15 @@ bool stag_group_applies(const OpDev& op, int prec, int kind, int npass);
 int stag_group_shape();
 cudaError_t launch_stag_group(const OpDev& op, int kind, const Engine& e, const PassDesc* d_descs, int npass,
                               cudaStream_t st, const int* act);
+// One FP32 system (PASS_A, PASS_B) with the links of each tile of sites
+// staged in shared memory by bulk asynchronous copies; stag_tile_fits() says
+// whether the lattice can be cut into such tiles (recon links only). A wait
+// on the copies that runs out after wait_ns sets bit 0 of *e.err; no_copy
+// issues none (a test of that path).
+bool stag_tile_fits(const StagGeom& g, int nc);
+size_t stag_tile_smem(int nc, int L0);
+cudaError_t launch_stag_tile(const OpDev& op, int kind, const Engine& e, const PassDesc* d_descs, uint64_t wait_ns,
+                             int no_copy, cudaStream_t st);
 // h_desc (optional): host copy of the single pass's descriptor; a one-system
 // FP32 PASS_A then takes its source and output pointers from it as kernel
 // parameters (the device descriptor must hold the same pointers).

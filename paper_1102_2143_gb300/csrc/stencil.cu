@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "async.cuh"
 #include "stencil.cuh"
 
 namespace msc {
@@ -86,6 +87,222 @@ cudaError_t launch_stag_pass(const OpDev& op, int prec, int kind, int out_f32, c
     }
     if (op.recon) return launch_kind<float, 2, 1>(kind, out_f32, e, d_descs, op.g, op.links32, npass, act, per, st);
     return launch_kind<float, 2, 0>(kind, out_f32, e, d_descs, op.g, op.links32, npass, act, per, st);
+}
+
+// ---------------------------------------------------------------------------
+// One FP32 system with the links staged in shared memory. The lattice is cut
+// into tiles of kTile consecutive sites (one per thread) lying inside one
+// x0-x1 plane (kTile divides L0 L1, L0 divides kTile). For a tile, one thread
+// issues bulk asynchronous copies of every link the tile's sites use: the
+// tile's own links in the four directions (the forward hops, and the
+// backward hops along x0, whose neighbour sits in the same row), the links
+// of the tile one plane below along x2 and along x3 (backward hops there),
+// and one row of x1 links below the tile (the backward x1 hop of its first
+// row). The copies complete on an mbarrier; the threads then apply D from
+// shared memory, reading the neighbour spinors (colour-planar) from global
+// memory. The link stream, 80% of a pass's bytes, is thus in flight in
+// 75 KB per tile without holding registers. A wait that runs out (bounded by
+// the global timer) marks the Engine's error word; the block skips its
+// remaining tiles but still takes part in the reduction, so the context's
+// counters stay consistent.
+// Opt-in (MSC_STAG_TILE=1): on the 32^4 solve it takes 66 / 76 us per pass
+// against 61 / 74 us for k_stag reading its links directly (and 92 / 114 us
+// double-buffered at one block per SM): the passes are bound by the latency
+// of the neighbour-spinor gathers at the resident warps, not by link bytes in
+// flight. It sums in k_stag's order, so its results are the same bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int kTile = kThreads;
+
+template <int NC> struct TileE { static constexpr int E = NC == 3 ? 3 : 1; };  // float4 per stored link
+
+// dynamic shared memory of a block: one tile's links
+size_t stag_tile_smem(int nc, int L0) {
+    const int E = nc == 3 ? 3 : 1;
+    return (size_t)(6 * E * kTile + E * L0) * 16;
+}
+
+bool stag_tile_fits(const StagGeom& g, int nc) {
+    const int P01 = g.L[0] * g.L[1];
+    return g.eo == 0 && kTile % g.L[0] == 0 && P01 % kTile == 0 && g.V >= kTile &&
+           stag_tile_smem(nc, g.L[0]) <= 76 * 1024;
+}
+
+// the link at shared-memory float4 index i (stride `st` between components)
+template <int NC>
+__device__ __forceinline__ void tile_link(const float4* __restrict__ p, int st, float2 (&u)[NC][NC]) {
+    if constexpr (NC == 3) {
+        const float4 q0 = p[0], q1 = p[st], q2 = p[2 * st];
+        u[0][0] = {q0.x, q0.y}; u[0][1] = {q0.z, q0.w};
+        u[0][2] = {q1.x, q1.y}; u[1][0] = {q1.z, q1.w};
+        u[1][1] = {q2.x, q2.y}; u[1][2] = {q2.z, q2.w};
+        u[2][0] = cconj(csub(cmul(u[0][1], u[1][2]), cmul(u[0][2], u[1][1])));
+        u[2][1] = cconj(csub(cmul(u[0][2], u[1][0]), cmul(u[0][0], u[1][2])));
+        u[2][2] = cconj(csub(cmul(u[0][0], u[1][1]), cmul(u[0][1], u[1][0])));
+    } else {
+        const float4 q = p[0];
+        u[0][0] = {q.x, q.y};
+        u[0][1] = {q.z, q.w};
+        u[1][0] = {-q.z, q.w};
+        u[1][1] = {q.x, -q.y};
+    }
+}
+
+template <int NC, int KIND>
+__global__ void __launch_bounds__(kThreads, 3)
+k_stag_tile(Engine e, const PassDesc* descs, StagGeom g, const float4* __restrict__ links, uint64_t wait_ns,
+            int no_copy) {
+    constexpr int E = TileE<NC>::E;
+    extern __shared__ float4 sl[];  // [4][E][T] forward, [E][T] back x2, [E][T] back x3, [E][L0] back x1 halo
+    __shared__ uint64_t bar;
+    __shared__ int s_bad;
+    const PassDesc d = descs[0];
+    if (gated_off(e, d)) return;
+    const int V = g.V, L0 = g.L[0], L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+    const int P01 = L0 * L1, P012 = P01 * L2;
+    const int ntiles = V / kTile;
+    float4* fw = sl;
+    float4* b2 = sl + 4 * E * kTile;
+    float4* b3 = b2 + E * kTile;
+    float4* b1 = b3 + E * kTile;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        s_bad = 0;
+    }
+    __syncthreads();
+    const float2* __restrict__ src = (const float2*)d.src;
+    const float2* __restrict__ aux = (const float2*)d.aux;
+    float2* out = (float2*)d.out;
+    const float dd = (float)d.d;
+    const float alpha = (KIND == PASS_B || KIND == PASS_BC) ? (float)e.sys[d.sys].alpha : 0.f;
+    double local = 0.0;
+    uint32_t parity = 0;
+    bool inflight = false;  // thread 0: copies issued and not waited for
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int s0 = tile * kTile;
+        if (threadIdx.x == 0) {
+            async_proxy_fence();  // the previous tile's reads before the copies overwrite
+            const uint32_t tb = kTile * 16, hb = (uint32_t)L0 * 16;
+            mbar_arrive_expect_tx(&bar, 6u * E * tb + E * hb);
+            if (!no_copy) {
+                const int c1 = (s0 / L0) % L1, c2 = (s0 / P01) % L2, c3 = s0 / P012;
+                const int h1 = c1 > 0 ? s0 - L0 : s0 + (L1 - 1) * L0;
+                const int t2 = c2 > 0 ? s0 - P01 : s0 + (L2 - 1) * P01;
+                const int t3 = c3 > 0 ? s0 - P012 : s0 + (L3 - 1) * P012;
+                for (int mu = 0; mu < 4; ++mu)
+                    for (int c = 0; c < E; ++c)
+                        bulk_copy_g2s(fw + (mu * E + c) * kTile, links + ((size_t)mu * E + c) * V + s0, tb, &bar);
+                for (int c = 0; c < E; ++c) {
+                    bulk_copy_g2s(b2 + c * kTile, links + ((size_t)2 * E + c) * V + t2, tb, &bar);
+                    bulk_copy_g2s(b3 + c * kTile, links + ((size_t)3 * E + c) * V + t3, tb, &bar);
+                    bulk_copy_g2s(b1 + c * L0, links + ((size_t)E + c) * V + h1, hb, &bar);
+                }
+                inflight = true;
+            }
+        }
+        if (mbar_wait_bounded(&bar, parity, wait_ns)) inflight = false;
+        else s_bad = 1;
+        parity ^= 1;
+        __syncthreads();
+        if (s_bad) break;
+        const int l = threadIdx.x;
+        const int x = s0 + l;
+        const SiteNbrs nb = neighbours(x, g);
+        float2 y[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) y[a] = {0.f, 0.f};
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            float2 u[NC][NC], w[NC][NC], v[NC], z[NC];
+#pragma unroll
+            for (int b = 0; b < NC; ++b) {
+                v[b] = src[(size_t)b * V + nb.fwd[mu]];
+                z[b] = src[(size_t)b * V + nb.bwd[mu]];
+            }
+            tile_link<NC>(fw + mu * E * kTile + l, kTile, u);
+            if (mu == 0) tile_link<NC>(fw + (nb.bwd[0] - s0), kTile, w);
+            else if (mu == 1) {
+                if (l >= L0) tile_link<NC>(fw + E * kTile + (l - L0), kTile, w);
+                else tile_link<NC>(b1 + l, L0, w);
+            } else if (mu == 2) tile_link<NC>(b2 + l, kTile, w);
+            else tile_link<NC>(b3 + l, kTile, w);
+            const float eta = nb.par[mu] ? -0.5f : 0.5f;
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                float2 f = {0.f, 0.f};
+#pragma unroll
+                for (int b = 0; b < NC; ++b) {
+                    cfma(f, u[a][b], v[b]);       // + U_mu(x) src(x+mu)
+                    cfms_conj(f, w[b][a], z[b]);  // - U_mu(x-mu)^dag src(x-mu)
+                }
+                y[a].x = fmaf(eta, f.x, y[a].x);
+                y[a].y = fmaf(eta, f.y, y[a].y);
+            }
+        }
+        float loc = 0.f;
+        if (KIND == PASS_A) {
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                out[(size_t)a * V + x] = y[a];
+                if (d.row >= 0) {
+                    const float2 pa = aux[(size_t)a * V + x];
+                    loc += dd * (pa.x * pa.x + pa.y * pa.y) + y[a].x * y[a].x + y[a].y * y[a].y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                const float2 pa = aux[(size_t)a * V + x];
+                float2 ra = out[(size_t)a * V + x];
+                ra.x -= alpha * (dd * pa.x - y[a].x);
+                ra.y -= alpha * (dd * pa.y - y[a].y);
+                out[(size_t)a * V + x] = ra;
+                loc += ra.x * ra.x + ra.y * ra.y;
+            }
+        }
+        local += (double)loc;
+        __syncthreads();  // every thread is done with this tile's links
+    }
+    if (s_bad && threadIdx.x == 0) {
+        if (e.err) atomicOr(e.err, 1u);
+        // copies still in flight complete on the barrier's open phase
+        if (inflight) mbar_wait_bounded(&bar, parity ^ 1, wait_ns);
+    }
+    if (d.row >= 0) {
+        double tot;
+        if (reduce_last_n(e, d.row, local, tot, gridDim.x, blockIdx.x)) finalize<KIND == PASS_BC>(e, d, tot);
+    }
+}
+
+template <int NC, int KIND>
+static cudaError_t launch_tile(const Engine& e, const PassDesc* descs, const StagGeom& g, const void* links,
+                               uint64_t wait_ns, int no_copy, cudaStream_t st) {
+    auto k = k_stag_tile<NC, KIND>;
+    const size_t sm = stag_tile_smem(NC, g.L[0]);
+    cudaError_t err = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, (const void*)k, kThreads, sm, 0) != cudaSuccess)
+        per_sm = 1;
+    const int ntiles = g.V / kTile;
+    const int grid = std::max(1, std::min(ntiles, std::max(1, per_sm) * std::max(1, sms)));
+    k<<<grid, kThreads, sm, st>>>(e, descs, g, (const float4*)links, wait_ns, no_copy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stag_tile(const OpDev& op, int kind, const Engine& e, const PassDesc* d_descs, uint64_t wait_ns,
+                             int no_copy, cudaStream_t st) {
+    const int k = (kind == PASS_B && e.cond_flag) ? PASS_BC : kind;
+    if (op.nc == 3) {
+        if (k == PASS_A) return launch_tile<3, PASS_A>(e, d_descs, op.g, op.links32, wait_ns, no_copy, st);
+        if (k == PASS_B) return launch_tile<3, PASS_B>(e, d_descs, op.g, op.links32, wait_ns, no_copy, st);
+        return launch_tile<3, PASS_BC>(e, d_descs, op.g, op.links32, wait_ns, no_copy, st);
+    }
+    if (k == PASS_A) return launch_tile<2, PASS_A>(e, d_descs, op.g, op.links32, wait_ns, no_copy, st);
+    if (k == PASS_B) return launch_tile<2, PASS_B>(e, d_descs, op.g, op.links32, wait_ns, no_copy, st);
+    return launch_tile<2, PASS_BC>(e, d_descs, op.g, op.links32, wait_ns, no_copy, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -50,9 +50,9 @@ def test_spmv_bytes_of_the_benchmark_operator():
 class _StagInfo:
     """Two right-hand sides x two shifts on the stencil path (see below)."""
     iters = 3
-    shift_iters = np.array([[3, 1], [2, 1]])
-    reliable_updates = 1
-    refine_reliable_updates = 0
+    shift_iters = np.array([[3, 1], [2, 1]], dtype=np.int32)
+    reliable_updates = 2
+    refine_reliable_updates = 1
     refine_rounds = 1
     shift_refine_iters = np.array([[0, 2], [0, 0]])
 
@@ -68,8 +68,10 @@ def test_stencil_solve_bytes_hand_worked_case():
       links of both passes, 3 iterations: 3 * 2 * 16 * 192     = 18432
       folds (1 reliable update + the final one per RHS) x 2 shifts x 40 * 3 * 16
                                                                 = 11520
-      the reliable update's FP64 residual 16 * 1416             = 22656
+      the stage's reliable update: FP64 residual 16 * 1416      = 22656
+      the refinement's reliable update: FP64 residual 22656 + the
+      fold of its one shift 40 * 3 * 16 = 1920                  = 24576
       checks (4 + 1 refined) * 16 * 1416                        = 113280
       refinement k = 1, 2: 2 * 16 * 192 + 16 * 11 * 24 each     = 20736
-      total 210048 B."""
-    assert bench.stencil_solve_bytes(_StagInfo(), 2, 16, 3, 1, mixed=True) == 210048
+      total 234624 B."""
+    assert bench.stencil_solve_bytes(_StagInfo(), 2, 16, 3, 1, mixed=True) == 234624
