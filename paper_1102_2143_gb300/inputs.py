@@ -1,9 +1,13 @@
 """Seeded synthetic inputs for the shifted-family solve (A + sigma_s) x_s = b.
 
-This module draws random numbers and nothing else: gauge links, sources, shift
-lists and generic Hermitian positive-definite block-sparse test matrices. It
-holds none of the solver's arithmetic and imports nothing from the CUDA
-library or from the oracle, so both sides can be fed the same inputs.
+This module draws the seeded inputs: gauge links, sources, shift lists and
+generic Hermitian positive-definite block-sparse test matrices. It holds none
+of the solver's arithmetic (no Krylov step, recurrence or residual) and
+imports nothing from the CUDA library or from the oracle, so both sides can be
+fed the same inputs. Two functions assemble an operator as block-CSR input
+for the generic path: the paper's five-point Poisson matrix
+(`poisson_5pt_bsr`) and the staggered Dirac matrix m + D (`staggered_dirac_bsr`);
+both are checked against the oracle's own operators in the CPU tests.
 
 Conventions (shared by every consumer of these arrays):
   * lattice dims = (L0, L1, L2, L3); site = x0 + L0*(x1 + L1*(x2 + L2*x3)),
