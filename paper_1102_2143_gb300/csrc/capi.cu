@@ -1041,7 +1041,13 @@ static int apply_impl(msc_ctx* c, const msc_op* op, double sigma, const double* 
         else CK(launch_convert(out32, 1, out64, 0, n, c->work));
     }
     CK(cudaMemcpyAsync(out, out64, n * 16, cudaMemcpyDefault, c->work));
+    CK(cudaMemcpyAsync(c->h_err, c->errf.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->work));
     CK(cudaStreamSynchronize(c->work));
+    if (*c->h_err) {  // a staged pass's bounded wait ran out: out is void
+        CK(cudaMemsetAsync(c->errf.p, 0, sizeof(unsigned), c->work));
+        CK(cudaStreamSynchronize(c->work));
+        return MSC_ERR_TIMEOUT;
+    }
     return MSC_OK;
 }
 

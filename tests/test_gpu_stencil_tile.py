@@ -72,6 +72,11 @@ def test_wait_that_runs_out_reports_timeout():
     with pytest.raises(msc.MscError) as e:
         msc.solve(c, op, torch.from_numpy(p.b).cuda(), p.sigma, tol=p.tol)
     assert e.value.code == msc.MSC_ERR_TIMEOUT
+    # the FP32 operator apply runs the same staged pass and reports it too
+    v = torch.from_numpy(p.b[0]).cuda()
+    with pytest.raises(msc.MscError) as e:
+        msc.msc_op_apply(c, op, 0.0, v, torch.empty_like(v), msc.MSC_FP32)
+    assert e.value.code == msc.MSC_ERR_TIMEOUT
     msc.msc_op_destroy(op)
     msc.msc_destroy(c)
     torch.cuda.synchronize()
