@@ -239,6 +239,29 @@ def test_generic_bsr_solve_ragged(ctx):
     msc.msc_op_destroy(bop)
 
 
+@pytest.mark.parametrize("nrhs", [5, 19])
+def test_generic_bsr_many_rhs_share_matrix(ctx, nrhs):
+    """Right-hand sides sharing a ragged block-CSR matrix (45 block rows: one
+    full slice and a ragged one) in mixed precision: each FP32 SpMV applies
+    the matrix to every system still iterating, two per thread, one group of
+    two per row of blocks (5 right-hand sides: three groups, the last half
+    empty; 19: ten groups), and the refinement does the same for the shifts
+    it refines. Every x_s against a dense FP64 solve."""
+    rp, ci, va, A = inputs.random_hpd_bsr(45, 3, 6, 0.05, 91)
+    n = A.shape[0]
+    B = np.stack([inputs.gaussian_source(n, 100 + r) for r in range(nrhs)])
+    sig = inputs.log_shifts(1e-3, 3.0, 4)
+    bop = msc.msc_op_bsr(ctx, 45, 3, rp, ci, va)
+    x, info = msc.solve(ctx, bop, B, sig, tol=1e-10, precision=msc.MSC_MIXED)
+    assert info.status == 0
+    for r in range(nrhs):
+        for s, sv in enumerate(sig):
+            M = A + sv * np.eye(n)
+            assert rel(x[r][s], np.linalg.solve(M, B[r])) <= 1e-8
+            assert np.linalg.norm(B[r] - M @ x[r][s]) <= 1e-10 * np.linalg.norm(B[r])
+    msc.msc_op_destroy(bop)
+
+
 def test_poisson_paper_operator_15_shifts(ctx):
     """The paper's own test operator (Sec. 4, Table 1): the 2-D five-point
     Poisson Laplacian, here on a 96 x 96 grid, 15 shifts 1e-4..10, through the
