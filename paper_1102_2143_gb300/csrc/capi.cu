@@ -781,8 +781,7 @@ int msc_op_staggered(msc_ctx* c, msc_op** out, int nc, const int dims[4], const 
     OpDev& d = op->dev;
     d.kind = OP_STAGGERED;
     d.nc = nc;
-    for (int mu = 0; mu < 4; ++mu) d.g.L[mu] = dims[mu];
-    d.g.V = (int)V;
+    d.g = stag_geom(dims);
     d.n = V * nc;
     d.mass = mass;
     const size_t nlink_bytes = (size_t)4 * V * nc * nc * 16;

@@ -26,9 +26,22 @@ struct StagGeom {
     // p = (x0 + x1 + x2 + x3) mod 2; its vectors hold those sites only, in
     // site order (compressed index x / 2), and D passes alternate parities.
     int eo = 0;
+    // Division by the divisors d_k = L0, L1, L2, L0 / 2 as a multiply-high
+    // (Granlund and Montgomery, "Division by invariant integers using
+    // multiplication", 1994): x / d_k = (umulhi(x, dm[k]) + x) >> ds[k] for
+    // 0 <= x < 2^31, with ds = ceil(log2 d) and dm = floor(2^(32+ds) / d) + 1
+    // - 2^32. Set by stag_geom().
+    unsigned dm[4];
+    int ds[4];
 };
 // sites a vector of the operator holds
 __host__ __device__ __forceinline__ int vlen(const StagGeom& g) { return g.eo ? (g.V >> 1) : g.V; }
+// x / d_k (see StagGeom::dm) for 0 <= x < 2^31
+__device__ __forceinline__ int gdiv(int x, const StagGeom& g, int k) {
+    return (int)((__umulhi((unsigned)x, g.dm[k]) + (unsigned)x) >> g.ds[k]);
+}
+// The geometry of a lattice of extents dims[0..3] (each >= 2, V < 2^31).
+StagGeom stag_geom(const int dims[4]);
 
 // Device-resident operator data.
 struct OpDev {

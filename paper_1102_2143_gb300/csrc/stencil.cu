@@ -21,6 +21,27 @@
 
 namespace msc {
 
+StagGeom stag_geom(const int dims[4]) {
+    StagGeom g;
+    int64_t V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        g.L[mu] = dims[mu];
+        V *= dims[mu];
+    }
+    g.V = (int)V;
+    const int div[4] = {dims[0], dims[1], dims[2], std::max(1, dims[0] / 2)};
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t d = (uint64_t)div[k];
+        int l = 0;
+        while (((uint64_t)1 << l) < d) ++l;
+        // M = floor(2^(32+l) / d) + 1 lies in (2^32, 2^33]; dm = M - 2^32
+        const uint64_t M = ((uint64_t)1 << (32 + l)) / d + 1;
+        g.dm[k] = (unsigned)(M - ((uint64_t)1 << 32));
+        g.ds[k] = l;
+    }
+    return g;
+}
+
 // One D pass over every site with the epilogue `KIND` (see PASS_* in engine.h),
 // for the systems of the pass list (see sys_block in common.cuh).
 // FP32 passes: at most 80 registers (three 256-thread blocks per SM); the

@@ -17,11 +17,11 @@ struct SiteNbrs {
 __device__ __forceinline__ SiteNbrs neighbours(int x, const StagGeom& g) {
     SiteNbrs nb;
     int c[4];
-    int rem = x;
-    c[0] = rem % g.L[0]; rem /= g.L[0];
-    c[1] = rem % g.L[1]; rem /= g.L[1];
-    c[2] = rem % g.L[2]; rem /= g.L[2];
-    c[3] = rem;
+    const int q0 = gdiv(x, g, 0), q1 = gdiv(q0, g, 1), q2 = gdiv(q1, g, 2);
+    c[0] = x - q0 * g.L[0];
+    c[1] = q0 - q1 * g.L[1];
+    c[2] = q1 - q2 * g.L[2];
+    c[3] = q2;
     int stride = 1, psum = 0;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
@@ -42,13 +42,12 @@ __device__ __forceinline__ int vsite(int x, const StagGeom& g) { return g.eo ? (
 
 __device__ __forceinline__ int eo_site(int h, int par, const StagGeom& g) {
     const int hl = g.L[0] >> 1;
-    const int row = h / hl;
+    const int row = gdiv(h, g, 3);
     const int k = h - row * hl;
-    int r = row;
-    const int c1 = r % g.L[1];
-    r /= g.L[1];
-    const int c2 = r % g.L[2];
-    const int c3 = r / g.L[2];
+    const int r1 = gdiv(row, g, 1), r2 = gdiv(r1, g, 2);
+    const int c1 = row - r1 * g.L[1];
+    const int c2 = r1 - r2 * g.L[2];
+    const int c3 = r2;
     return 2 * k + ((par + c1 + c2 + c3) & 1) + g.L[0] * row;
 }
 
