@@ -266,14 +266,22 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int grou
     }
 }
 
+// Block shape of k_bsr_a1: 288 threads, four blocks per SM (36 warps, at most
+// 56 registers). A thread takes rows blockDim.x * gridDim.x apart, so the
+// rows per thread are nbr / (36 x 32 x SMs): 1.9 on the 24^4 matrix, where
+// 256 x 5 (40 warps) gives 1.7 and the last 30% of the rows run with 70% of
+// the warps (live SpMV 146.7 us against 152.4 us; 224 x 5 and 192 x 6:
+// 146.8 / 147.2 us; 256 x 4: 159.3 us).
+constexpr int kA1Threads = 288, kA1Blocks = 4;
+
 // The FP32 PASS_A of a single system with its source and output passed as
 // kernel parameters (the descriptor still gives the shift, gating and
 // reduction): the addresses come from the constant bank instead of
-// registers, which at five blocks per SM lets the row loop keep its loads in
-// flight (24^4: 142 us against 150 us with the pointers read from the
-// descriptor).
+// registers, which leaves the row loop the registers for its loads in
+// flight (24^4, at 256 x 5: 142 us against 150 us with the pointers read
+// from the descriptor).
 template <int BD>
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kA1Threads, kA1Blocks)
 k_bsr_a1(Engine e, const PassDesc* descs, OpDev A, const float2* __restrict__ vals,
          const float2* __restrict__ src, float2* __restrict__ out) {
     const PassDesc d = descs[0];
@@ -322,8 +330,10 @@ template <int BD>
 static void launch_a1(const Engine& e, const PassDesc* descs, const OpDev& A, const PassDesc& h,
                       cudaStream_t st) {
     auto k = k_bsr_a1<BD>;
-    k<<<resident_grid((const void*)k, A.nbr), kThreads, 0, st>>>(e, descs, A, A.vals32, (const float2*)h.src,
-                                                                  (float2*)h.out);
+    const int64_t need = (A.nbr + kA1Threads - 1) / kA1Threads;
+    const int grid =
+        (int)std::max<int64_t>(1, std::min<int64_t>(resident_blocks((const void*)k, kA1Threads), need));
+    k<<<grid, kA1Threads, 0, st>>>(e, descs, A, A.vals32, (const float2*)h.src, (float2*)h.out);
 }
 
 template <class T, int BD, int KIND, class TO>

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "engine.h"
@@ -461,6 +462,25 @@ int resident_grid(const void* fn, int64_t work) {
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
+}
+
+int resident_blocks(const void* fn, int threads) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({fn, dev, threads});
+    if (it != cache.end()) return it->second;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int cap = std::min(std::max(1, per_sm) * std::max(1, sms), kMaxBlocks);
+    cache[{fn, dev, threads}] = cap;
+    return cap;
 }
 
 dim3 multi_grid(const void* fn, int64_t work, int nsys, bool per_system) {

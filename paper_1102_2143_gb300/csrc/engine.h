@@ -224,6 +224,9 @@ int grid_blocks(int64_t work, int num_sms);
 // Blocks of kThreads for `work` items: one item per thread, capped at the
 // blocks that fit on the device at once for kernel `fn` (no partial waves).
 int resident_grid(const void* fn, int64_t work);
+// Blocks of `threads` threads resident on the device for kernel `fn`
+// (occupancy x SMs), at most kMaxBlocks.
+int resident_blocks(const void* fn, int threads);
 // Grid for `nsys` systems of `work` items each (see sys_block): 1-D, the
 // resident blocks and at least one per system; or, per_system, a full row
 // of resident blocks for every system.
