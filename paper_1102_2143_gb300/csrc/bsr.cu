@@ -170,6 +170,17 @@ k_bsr(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A, const
     }
 }
 
+// Block shape of the FP32 SpMVs k_bsr_a1 and k_bsr_multi: 288 threads, four
+// blocks per SM (36 warps, at most 56 registers). A thread takes rows
+// blockDim.x * gridDim.x (per group of systems) apart, so the rows per
+// thread are nbr / (36 x 32 x SMs) per group: 1.9 on the 24^4 matrix for
+// one group, 3.8 for two, where 256 x 5 (40 warps) gives 1.7 and 3.4 and the
+// last rows run on a part of the warps (24^4 solve: one-system SpMV 146.7 us
+// against 152.4 us live, 224 x 5 and 192 x 6: 146.8 / 147.2 us, 256 x 4:
+// 159.3 us; with the shared-matrix SpMV at this shape as well, the solve
+// takes 242.6 against 244.7 ms, and that kernel no longer spills).
+constexpr int kSpmvThreads = 288, kSpmvBlocks = 4;
+
 // y_j = (A + d_j) src_j for up to G systems j sharing the matrix: each block
 // value and column index is read once per thread and applied to every system
 // of its group (the refinement stage and several right-hand sides). Epilogue
@@ -183,7 +194,7 @@ k_bsr(Engine e, const PassDesc* descs, int npass, const int* act, OpDev A, const
 // `act` (optional): the passes still to run, act[0] = their count and
 // act[1..] their indices, so that groups stay full as systems finish.
 template <class T, int BD, int G>
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocks)
 k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int groups, OpDev A,
             const T2<T>* __restrict__ vals) {
     __shared__ PassDesc sd[G];
@@ -266,14 +277,6 @@ k_bsr_multi(Engine e, const PassDesc* descs, int npass, const int* act, int grou
     }
 }
 
-// Block shape of k_bsr_a1: 288 threads, four blocks per SM (36 warps, at most
-// 56 registers). A thread takes rows blockDim.x * gridDim.x apart, so the
-// rows per thread are nbr / (36 x 32 x SMs): 1.9 on the 24^4 matrix, where
-// 256 x 5 (40 warps) gives 1.7 and the last 30% of the rows run with 70% of
-// the warps (live SpMV 146.7 us against 152.4 us; 224 x 5 and 192 x 6:
-// 146.8 / 147.2 us; 256 x 4: 159.3 us).
-constexpr int kA1Threads = 288, kA1Blocks = 4;
-
 // The FP32 PASS_A of a single system with its source and output passed as
 // kernel parameters (the descriptor still gives the shift, gating and
 // reduction): the addresses come from the constant bank instead of
@@ -281,7 +284,7 @@ constexpr int kA1Threads = 288, kA1Blocks = 4;
 // flight (24^4, at 256 x 5: 142 us against 150 us with the pointers read
 // from the descriptor).
 template <int BD>
-__global__ void __launch_bounds__(kA1Threads, kA1Blocks)
+__global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocks)
 k_bsr_a1(Engine e, const PassDesc* descs, OpDev A, const float2* __restrict__ vals,
          const float2* __restrict__ src, float2* __restrict__ out) {
     const PassDesc d = descs[0];
@@ -330,10 +333,10 @@ template <int BD>
 static void launch_a1(const Engine& e, const PassDesc* descs, const OpDev& A, const PassDesc& h,
                       cudaStream_t st) {
     auto k = k_bsr_a1<BD>;
-    const int64_t need = (A.nbr + kA1Threads - 1) / kA1Threads;
+    const int64_t need = (A.nbr + kSpmvThreads - 1) / kSpmvThreads;
     const int grid =
-        (int)std::max<int64_t>(1, std::min<int64_t>(resident_blocks((const void*)k, kA1Threads), need));
-    k<<<grid, kA1Threads, 0, st>>>(e, descs, A, A.vals32, (const float2*)h.src, (float2*)h.out);
+        (int)std::max<int64_t>(1, std::min<int64_t>(resident_blocks((const void*)k, kSpmvThreads), need));
+    k<<<grid, kSpmvThreads, 0, st>>>(e, descs, A, A.vals32, (const float2*)h.src, (float2*)h.out);
 }
 
 template <class T, int BD, int KIND, class TO>
@@ -364,8 +367,10 @@ static void launch_multi_g(const Engine& e, const PassDesc* descs, int npass, co
                            const OpDev& A, cudaStream_t st) {
     auto k = k_bsr_multi<float, BD, G>;
     // row blocks interleaved with groups in x
-    const int nb = std::max(1, resident_grid((const void*)k, A.nbr) / groups);
-    k<<<nb * groups, kThreads, 0, st>>>(e, descs, npass, act, groups, A, A.vals32);
+    const int64_t need = (A.nbr + kSpmvThreads - 1) / kSpmvThreads;
+    const int nb = (int)std::max<int64_t>(
+        1, std::min<int64_t>(resident_blocks((const void*)k, kSpmvThreads) / groups, need));
+    k<<<nb * groups, kSpmvThreads, 0, st>>>(e, descs, npass, act, groups, A, A.vals32);
 }
 
 template <int BD>

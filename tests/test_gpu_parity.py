@@ -239,6 +239,26 @@ def test_generic_bsr_solve_ragged(ctx):
     msc.msc_op_destroy(bop)
 
 
+@pytest.mark.parametrize("bd,nbr", [(1, 613), (2, 301)])
+def test_generic_bsr_one_rhs_small_blocks(ctx, bd, nbr):
+    """One right-hand side on 1x1 and 2x2 complex blocks, mixed precision:
+    the one-system FP32 SpMV (288-thread blocks, rows a grid's width apart)
+    on block-row counts that fill neither a block nor a slice; every x_s
+    against a dense FP64 solve."""
+    rp, ci, va, A = inputs.random_hpd_bsr(nbr, bd, 7, 0.1, 500 + bd)
+    n = A.shape[0]
+    b = inputs.gaussian_source(n, 501 + bd)
+    sig = inputs.log_shifts(1e-3, 3.0, 5)
+    bop = msc.msc_op_bsr(ctx, nbr, bd, rp, ci, va)
+    x, info = msc.solve(ctx, bop, b, sig, tol=1e-10, precision=msc.MSC_MIXED)
+    assert info.status == 0
+    for s, sv in enumerate(sig):
+        M = A + sv * np.eye(n)
+        assert rel(x[s], np.linalg.solve(M, b)) <= 1e-8
+        assert np.linalg.norm(b - M @ x[s]) <= 1e-10 * np.linalg.norm(b)
+    msc.msc_op_destroy(bop)
+
+
 @pytest.mark.parametrize("nrhs", [5, 19])
 def test_generic_bsr_many_rhs_share_matrix(ctx, nrhs):
     """Right-hand sides sharing a ragged block-CSR matrix (45 block rows: one
