@@ -59,13 +59,13 @@ k_stag(Engine e, const PassDesc* descs, int npass, const int* act, StagGeom g, c
     const PassDesc d = descs[q.j];
     if (gated_off(e, d)) return;
     const T alpha = (KIND == PASS_B || KIND == PASS_BC) ? (T)e.sys[d.sys].alpha : T(0);
-    double local = 0.0;
+    SiteAcc<T, KIND> local = 0;
     const int nh = vlen(g);
     for (int h = q.bx * blockDim.x + threadIdx.x; h < nh; h += q.gx * blockDim.x)
         local += stag_site<T, NC, RECON, KIND, TO, true>(d, g, links, alpha, pass_site<KIND == PASS_A>(h, g));
     if (d.row >= 0) {
         double tot;
-        if (reduce_last_n(e, d.row, local, tot, q.gx, q.bx)) finalize<KIND == PASS_BC>(e, d, tot);
+        if (reduce_last_n(e, d.row, (double)local, tot, q.gx, q.bx)) finalize<KIND == PASS_BC>(e, d, tot);
     }
 }
 
@@ -384,9 +384,9 @@ k_stag_group(Engine e, const PassDesc* descs, int npass, const int* act, StagGeo
     for (int r = 0; r < NR; ++r) mask |= son[r] ? (1u << r) : 0u;
     if (mask == 0) return;
     const int V = vlen(g);  // sites (and colour-plane stride) of the vectors
-    double local[NR];
+    float local[NR];  // per-thread partial sums in FP32 (see SiteAcc)
 #pragma unroll
-    for (int r = 0; r < NR; ++r) local[r] = 0.0;
+    for (int r = 0; r < NR; ++r) local[r] = 0.f;
     for (int h = bx * blockDim.x + threadIdx.x; h < V; h += gx * blockDim.x) {
         const int x = pass_site<KIND == PASS_A>(h, g);
         const SiteNbrs nb = neighbours(x, g);
@@ -459,7 +459,7 @@ k_stag_group(Engine e, const PassDesc* descs, int npass, const int* act, StagGeo
                     loc += ra.x * ra.x + ra.y * ra.y;
                 }
             }
-            local[r] += (double)loc;
+            local[r] += loc;
         }
     }
     if (sd[0].row < 0) return;  // apply-only passes reduce nothing
@@ -467,7 +467,7 @@ k_stag_group(Engine e, const PassDesc* descs, int npass, const int* act, StagGeo
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const double v = warp_sum(local[r]);
+        const double v = warp_sum((double)local[r]);
         if (lane == 0) sred[r][w] = v;
     }
     __syncthreads();

@@ -3,6 +3,8 @@
 //   D_xy = 1/2 sum_mu eta_mu(x) [U_mu(x) d_{y,x+mu} - U_mu(x-mu)^dagger d_{y,x-mu}],
 //   eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}), periodic boundaries.
 #pragma once
+#include <type_traits>
+
 #include "engine.h"
 
 namespace msc {
@@ -155,8 +157,14 @@ __device__ __forceinline__ void dslash_site(const void* links, const T2<T>* __re
 //   PASS_C: out = b - (d aux - y) (FP64);  |out|^2
 //   PASS_D: out = d aux - y
 // PL: FP32 vectors (of type T or TO) are colour-planar (see vix).
+// A site's share of a pass's reduction: FP32 for the FP32 passes (summed
+// over a thread's sites in FP32, then reduced in FP64 across threads), FP64
+// for the residual pass and FP64 operators.
+template <class T, int KIND>
+using SiteAcc = typename std::conditional<(sizeof(T) == 4 && KIND != PASS_C), float, double>::type;
+
 template <class T, int NC, int RECON, int KIND, class TO, bool PL = false>
-__device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g, const void* links,
+__device__ __forceinline__ SiteAcc<T, KIND> stag_site(const PassDesc& d, const StagGeom& g, const void* links,
                                             T alpha, int x) {
     const T2<T>* __restrict__ src = (const T2<T>*)d.src;
     const T2<T>* __restrict__ aux = (const T2<T>*)d.aux;
@@ -176,7 +184,7 @@ __device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g
                 loc += dd * (pa.x * pa.x + pa.y * pa.y) + y[a].x * y[a].x + y[a].y * y[a].y;
             }
         }
-        return (double)loc;
+        return (SiteAcc<T, KIND>)loc;
     } else if (KIND == PASS_B || KIND == PASS_BC) {
         T2<T>* r = (T2<T>*)d.out;
         T loc = T(0);
@@ -190,7 +198,7 @@ __device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g
             r[vix<T, PL, NC>(x, a, V)] = ra;
             loc += ra.x * ra.x + ra.y * ra.y;
         }
-        return (double)loc;
+        return (SiteAcc<T, KIND>)loc;
     } else if (KIND == PASS_C) {
         TO* out = (TO*)d.out;
         double loc = 0.0;
@@ -215,7 +223,7 @@ __device__ __forceinline__ double stag_site(const PassDesc& d, const StagGeom& g
             const T2<T> xa = aux[vix<T, PL, NC>(x, a, V)];
             out[vix<T, PL, NC>(x, a, V)] = {dd * xa.x - y[a].x, dd * xa.y - y[a].y};
         }
-        return 0.0;
+        return SiteAcc<T, KIND>(0);
     }
 }
 
