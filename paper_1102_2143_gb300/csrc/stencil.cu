@@ -69,10 +69,36 @@ k_stag(Engine e, const PassDesc* descs, int npass, const int* act, StagGeom g, c
     }
 }
 
+static int device_sms() {
+    static const int n = [] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(1, sms);
+    }();
+    return n;
+}
+
 template <class T, int NC, int RECON, int KIND, class TO>
 static void launch_one(const Engine& e, const PassDesc* descs, StagGeom g, const void* links, int npass,
                        const int* act, bool per, cudaStream_t st) {
     auto k = k_stag<T, NC, RECON, KIND, TO>;
+    if constexpr (sizeof(T) == 8) {
+        // FP64 passes over few sites: smaller blocks, so that the FP64
+        // arithmetic (about 1/64 of the FP32 rate on GB300) spreads over more
+        // SMs; a 4^4 lattice's 256 sites in one 256-thread block would run on
+        // one SM (a one-thread-per-site pass keeps one site per thread).
+        const int64_t V = vlen(g);
+        const int np = std::max(npass, 1);
+        int nt = kThreads;
+        while (nt > 32 && ((V + nt - 1) / nt) * np < 2 * device_sms()) nt >>= 1;
+        if (nt < kThreads) {
+            const int per_sys = (int)((V + nt - 1) / nt);
+            const dim3 grid = (per && npass > 1) ? dim3(per_sys, npass) : dim3(per_sys * np);
+            k<<<grid, nt, 0, st>>>(e, descs, npass, act, g, links);
+            return;
+        }
+    }
     k<<<multi_grid((const void*)k, vlen(g), npass, per), kThreads, 0, st>>>(e, descs, npass, act, g, links);
 }
 
