@@ -513,9 +513,31 @@ cudaError_t launch_init_from_r(int prec, const Engine& e, const VecSet& v, int n
     return cudaGetLastError();
 }
 
+static int device_sms() {
+    static const int n = [] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(1, sms);
+    }();
+    return n;
+}
+
 cudaError_t launch_update(int prec, const Engine& e, const VecSet& v, int nsys, cudaStream_t st, const int* act) {
-    if (prec == PREC_F32) k_update<float><<<vgrid(k_update<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, nsys, act);
-    else k_update<double><<<vgrid(k_update<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, nsys, act);
+    if (prec == PREC_F32) {
+        k_update<float><<<vgrid(k_update<float>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, nsys, act);
+        return cudaGetLastError();
+    }
+    // FP64 update of a small system: blocks of fewer threads, so that its
+    // FP64 arithmetic spreads over more SMs (as for the FP64 stencil passes)
+    const int64_t work = (upv_of(prec, v) + kUnits - 1) / kUnits;
+    const int np = std::max(nsys, 1);
+    int nt = kThreads;
+    while (nt > 32 && ((work + nt - 1) / nt) * np < 2 * device_sms()) nt >>= 1;
+    if (nt < kThreads)
+        k_update<double><<<(unsigned)(((work + nt - 1) / nt) * np), nt, 0, st>>>(e, v, nsys, act);
+    else
+        k_update<double><<<vgrid(k_update<double>, upv_of(prec, v), kUnits, nsys), kThreads, 0, st>>>(e, v, nsys, act);
     return cudaGetLastError();
 }
 
